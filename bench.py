@@ -1,0 +1,279 @@
+#!/usr/bin/env python3
+"""Benchmark of the operator-split reaction-diffusion step on GB300.
+
+Workload: jittered 100x10x10 um box of 294,780 tets, random 10-species /
+20-reaction network, densities 1-100 /um^3, tau = 0.203 ms. One benchmark
+step = one steps_run call advancing the simulation by 20 ms (98 full windows
+and one shortened window = 99 launches of the fused step kernel, replayed
+from CUDA graphs). Metric: tet-updates/s = tets x windows / time.
+
+  value     device time (CUDA events on the simulation's stream) of K steps,
+            state resident in HBM; L2 flushed (256 MiB write) before each step,
+            outside the timed events.
+  e2e       the same metric through the public C ABI with host buffers:
+            steps_set_counts_all (H2D), steps_run, steps_get_counts_all (D2H),
+            wall clock per step.
+  roofline  the step kernel: algorithmic bytes per launch / average launch time.
+  cpu_baseline  the CPU oracle (serial C, 1 core) on a bounded sample.
+
+--impl reference runs the CPU oracle as the reference arm.
+With torchrun (N > 1) every rank runs an independent replica on its own GPU
+(different seed): weak scaling, value = sum over ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tet-updates/s"
+UNIT = "tet-updates/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_rate(w, windows: int):
+    """Serial oracle on `windows` full windows of the workload (1 core)."""
+    import oracle
+    o = oracle.from_workload(w, prec=64)
+    t0 = time.perf_counter()
+    for _ in range(windows):
+        o.step(o.tau)
+    dt = time.perf_counter() - t0
+    return w.n_tets * windows / dt, dt
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle.build import build as build_oracle
+    build_oracle()
+    from paper_1610_02258_gb300 import inputs as I
+    w = I.config2()
+    windows = 5
+    for _ in range(args.warmup):
+        oracle_rate(w, 1)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_rate(w, windows)
+        times.append(dt)
+    value = w.n_tets * windows * args.steps / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "tets": w.n_tets, "species": w.model.n_species,
+                   "reactions": w.model.n_reac, "sample": f"{windows} full windows per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{windows} full windows of {w.name} per step, serial C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1610_02258_gb300.build import build
+    build()
+    from paper_1610_02258_gb300 import capi
+    from paper_1610_02258_gb300 import inputs as I
+
+    w = I.config2(seed=3 + rank)
+    stream = torch.cuda.current_stream()
+    sim = capi.from_workload(w, cuda_stream=stream.cuda_stream)
+    tau = sim.tau
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    t_step = w.t_end
+
+    def step():
+        sim.run(sim.time + t_step)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    w0, l0 = capi.steps_get_windows(sim._sim)
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    w1, l1 = capi.steps_get_windows(sim._sim)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    windows = w1 - w0
+    units = w.n_tets * windows
+    if world > 1:
+        t = torch.tensor([ms, float(units)], device="cuda", dtype=torch.float64)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        ms_all, units_all = float(tmax[0]), float(t[1])
+    else:
+        ms_all, units_all = ms, float(units)
+    value = units_all / (ms_all / 1e3)
+
+    # end to end through the C ABI with host buffers
+    host_in = np.ascontiguousarray(w.counts, np.int32)
+    host_out = np.empty_like(host_in)
+    e2e_steps = max(3, min(args.steps, 10))
+    t_e = []
+    we0, _ = capi.steps_get_windows(sim._sim)
+    for _ in range(e2e_steps):
+        t0 = time.perf_counter()
+        capi.steps_set_counts_all(sim._sim, host_in)
+        step()
+        capi.steps_get_counts_all(sim._sim, w.model.n_species, w.n_tets, host_out)
+        t_e.append(time.perf_counter() - t0)
+    we1, _ = capi.steps_get_windows(sim._sim)
+    e2e_units = w.n_tets * (we1 - we0)
+    e2e = {"value": e2e_units / sum(t_e), "unit": UNIT, "h2d_bytes_per_step": int(host_in.nbytes),
+           "d2h_bytes_per_step": int(host_out.nbytes)}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+        return
+    S = w.model.n_species
+    bytes_per_tet = 8 * S + 36
+    kernel_s = (ms / 1e3) / windows
+    achieved = w.n_tets * bytes_per_tet / kernel_s / 1e9
+    peak, peak_kind = _peaks()
+    prof = os.path.join(ROOT, "profiles", "traffic_step_kernel_config2.json")
+    traffic = None
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+fp32", "data": "synthetic",
+        "config": {"workload": w.name, "tets": w.n_tets, "species": S, "reactions": w.model.n_reac,
+                   "tau_ms": tau * 1e3, "sim_ms_per_step": t_step * 1e3,
+                   "windows_per_step": windows / args.steps, "form": "plain",
+                   "l2": "flushed before each timed step (256 MiB write, outside the events)",
+                   "parallelism": f"replicas{world}"},
+        "e2e": e2e,
+        "gpu_launches": int(l1 - l0),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_source": peak_kind,
+                     "bytes_per_tet_update": bytes_per_tet, "kernel_us_avg": kernel_s * 1e6},
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cpu_windows = args.cpu_windows
+        rate, dt = oracle_rate(w, cpu_windows)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{cpu_windows} full windows of {w.name} ({dt:.1f} s), serial C, FP64"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-windows", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

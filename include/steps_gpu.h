@@ -1,0 +1,171 @@
+/*
+ * steps_gpu.h -- C ABI of the GB300 operator-splitting reaction-diffusion
+ * library (Parallel STEPS method, Chen & De Schutter).
+ *
+ * The method (§2, Algorithm 1): a tetrahedral mesh, a set of species with
+ * diffusion constants and a set of mass-action reactions. Time advances in
+ * windows of constant length tau = 1 / max_{S,tet} d_{S,tet} (§2.1). In every
+ * window each tet first runs its own reactions by Gillespie's SSA for tau,
+ * tracking each species' time-averaged occupancy; then, for every diffusive
+ * species, a binomial number of molecules leaves the tet and is split over
+ * its face neighbours in proportion to the face rates D*A/(V*d) (Algorithm 1,
+ * diffusion operator). All tets advance together on one GPU.
+ *
+ * Conventions for every call:
+ *   - Return 0 on success or a negative STEPS_ERR_* code; nothing aborts.
+ *     steps_last_error() returns a thread-local message for the last failure.
+ *   - Arrays passed in are owned by the caller and copied before the call
+ *     returns (unless stated otherwise); handles are owned by the library
+ *     until the matching *_destroy.
+ *   - Tet indices are always the caller's original order (the library may
+ *     reorder tets internally for locality; results do not depend on it).
+ *   - Host pointers unless a name ends in _device (CUDA device pointers).
+ *   - A NULL handle or array, or a size out of range, gives STEPS_ERR_ARG.
+ *   - Units: metres, seconds, m^2/s; rate constants in SI (order 0: M/s,
+ *     order 1: 1/s, order 2: 1/(M s)).
+ */
+#ifndef STEPS_GPU_H
+#define STEPS_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STEPS_OK 0
+#define STEPS_ERR_ARG (-1)     /* bad argument */
+#define STEPS_ERR_MESH (-2)    /* invalid mesh (degenerate tet, face of 3+ tets, bad index) */
+#define STEPS_ERR_MODEL (-3)   /* invalid model (order > 2, negative rate, too many species) */
+#define STEPS_ERR_OOM (-4)     /* device or host allocation failed */
+#define STEPS_ERR_CUDA (-5)    /* a CUDA call failed */
+#define STEPS_ERR_TIMEOUT (-6) /* a bounded device wait ran out (the window's results are not valid) */
+#define STEPS_ERR_STATE (-7)   /* device-side check failed (negative count) or bad call order */
+
+#define STEPS_MAX_SPECIES 32
+#define STEPS_MAX_REACTIONS 32
+
+typedef struct steps_mesh steps_mesh;
+typedef struct steps_model steps_model;
+typedef struct steps_sim steps_sim;
+
+/* Occupancy modes of the trial count fed to the diffusion operator. */
+#define STEPS_OCC_MEAN 1 /* Algorithm 1: mean occupancy Nbar = O_S / tau, stochastically rounded (default) */
+#define STEPS_OCC_END 0  /* end-of-reaction-phase count */
+
+/* Internal tet order. */
+#define STEPS_REORDER_NONE 0
+#define STEPS_REORDER_MORTON 1 /* Morton (Z-order) of barycentres (default) */
+
+typedef struct steps_options {
+    int32_t occupancy;   /* STEPS_OCC_MEAN or STEPS_OCC_END */
+    int32_t reorder;     /* STEPS_REORDER_* */
+    int32_t block;       /* threads per block of the step kernel; 0 = default (256) */
+    int32_t use_graph;   /* 1 = replay full windows from a captured CUDA graph (default), 0 = plain launches */
+    int32_t reserved[4]; /* set to 0 */
+} steps_options;
+
+/* Fill *opt with the defaults. */
+void steps_options_default(steps_options *opt);
+
+/*
+ * Mesh from vertices and tets (§2.1: the geometry every process is given).
+ *   verts_xyz: [nv*3] float64, metres, row-major (x, y, z).
+ *   tets:      [nt*4] int32, 0-based vertex indices. Local face f of a tet is
+ *              the face opposite its local vertex f.
+ * Builds face adjacency (faces matched by vertex triple), volumes V, face
+ * areas A and barycentre distances d, and the geometric face rates
+ * g_f = A_f / (V d_f) in float64. Boundary faces are reflective.
+ * Errors: STEPS_ERR_ARG (nv < 4, nt < 1, NULL), STEPS_ERR_MESH (index out of
+ * range, zero-volume tet, a face shared by more than two tets).
+ */
+int steps_mesh_create(const double *verts_xyz, int64_t nv, const int32_t *tets, int64_t nt,
+                      steps_mesh **out);
+void steps_mesh_destroy(steps_mesh *mesh);
+/* Number of tets of the mesh. */
+int steps_mesh_num_tets(const steps_mesh *mesh, int64_t *nt);
+
+/*
+ * Model: species and mass-action reactions (§2.1 "biochemical model").
+ *   diff_m2_per_s: [n_species] diffusion constants, 0 = immobile.
+ *   lhs, rhs:      [n_reac * n_species] int32 reactant / product molecule
+ *                  counts of each reaction (row r = reaction r).
+ *   k:             [n_reac] rate constants (order 0: M/s, 1: 1/s, 2: 1/(M s)).
+ * Propensities per tet of volume V (litres V_L): order 0 a = k N_A V_L;
+ * order 1 a = k N_X; order 2 a = k/(N_A V_L) N_X N_Y, and for X + X,
+ * a = k/(N_A V_L) N_X (N_X - 1).
+ * Errors: STEPS_ERR_ARG (n_species not in [1, 32], n_reac not in [0, 32]),
+ * STEPS_ERR_MODEL (negative D, k or stoichiometry, reaction order > 2, more
+ * than 6 species changed by one reaction).
+ */
+int steps_model_create(int32_t n_species, const double *diff_m2_per_s, int32_t n_reac,
+                       const int32_t *lhs, const int32_t *rhs, const double *k, steps_model **out);
+void steps_model_destroy(steps_model *model);
+
+/*
+ * Simulation of `model` on `mesh`, state resident on the current CUDA device.
+ *   seed:        key of the counter-based Philox4x32-10 stream; every draw is
+ *                addressed by (window, original tet id, purpose, index), so
+ *                results do not depend on tet order, launch shape or batching.
+ *   opt:         NULL = defaults.
+ *   cuda_stream: cudaStream_t to launch on (NULL = the legacy default stream).
+ * Computes tau = 1 / (max_S D_S * max_tet G_tet) over diffusive species
+ * (§2.1; +inf when nothing can diffuse, in which case every steps_run call
+ * is a single reaction window), the fixed-point face thresholds and the
+ * per-tet volume factors, and uploads them. Counts start at zero.
+ * The mesh and model may be destroyed after this call.
+ */
+int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t seed,
+                     const steps_options *opt, void *cuda_stream, steps_sim **out);
+void steps_sim_destroy(steps_sim *sim);
+
+/* Counts of one species in every tet: counts[nt] int32 >= 0, original tet order (host). */
+int steps_set_counts(steps_sim *sim, int32_t species, const int32_t *counts);
+int steps_get_counts(const steps_sim *sim, int32_t species, int32_t *out);
+/* All species at once: [n_species * nt] int32, species-major (host). */
+int steps_set_counts_all(steps_sim *sim, const int32_t *counts);
+int steps_get_counts_all(const steps_sim *sim, int32_t *out);
+
+/*
+ * Restrict reaction `reac` to the tets with active[tet] != 0 (original tet
+ * order, [nt] uint8; NULL = active everywhere). Used for region-limited
+ * sources such as a zero-order influx.
+ */
+int steps_set_reac_mask(steps_sim *sim, int32_t reac, const uint8_t *active);
+
+/*
+ * Advance from the current time t to t_end (Algorithm 1 main loop).
+ * Full windows of tau while t + tau <= t_end (within 1e-9 tau); a shorter
+ * last window tau_k = t_end - t if time remains; tau is unchanged for later
+ * calls (a run that stops off the window grid restarts the grid at t_end).
+ * Time is t_base + k tau, recomputed, not accumulated. t_end <= t is a no-op.
+ * Returns STEPS_ERR_ARG for a non-finite t_end and STEPS_ERR_STATE if a
+ * device-side check failed (a negative count, or a tet that fired more than
+ * 2^24 reactions in one window, which stops that tet's reaction phase).
+ * The call returns after the work is enqueued on the stream and the error
+ * word read back (so it synchronises with the stream once per call).
+ */
+int steps_run(steps_sim *sim, double t_end);
+
+int steps_get_time(const steps_sim *sim, double *t);
+int steps_get_tau(const steps_sim *sim, double *tau);
+/* Windows run so far (the RNG window index) and kernel launches issued. */
+int steps_get_windows(const steps_sim *sim, uint64_t *windows, uint64_t *launches);
+
+const char *steps_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Test hooks: run one device building block on host arrays.              */
+/* ---------------------------------------------------------------------- */
+
+/* Philox4x32-10 on the device: out[4*i..] = philox(key = seed, counter =
+ * ctr[4*i..]), n counters. Host arrays in and out. */
+int steps_debug_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out);
+/* The step kernel's float natural logarithm on the device, n values. */
+int steps_debug_logf(const float *x, int64_t n, float *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STEPS_GPU_H */

@@ -61,6 +61,8 @@ def lib():
         L.orc_logf32.restype = ctypes.c_float
         L.orc_sample_faces.argtypes = [c_u64, c_u64, c_u32, c_u32, c_i32, P, P]
         L.orc_sample_faces.restype = c_u32
+        L.orc_logf32_array.argtypes = [P, c_i64, P]
+        L.orc_philox_array.argtypes = [c_u64, P, c_i64, P]
         _lib = L
     return _lib
 
@@ -96,6 +98,20 @@ def philox(key, ctr):
 
 def logf32(x: float) -> float:
     return float(lib().orc_logf32(ctypes.c_float(x)))
+
+
+def logf32_array(x):
+    a = np.ascontiguousarray(x, np.float32)
+    out = np.empty_like(a)
+    lib().orc_logf32_array(_p(a), a.size, _p(out))
+    return out
+
+
+def philox_array(seed, ctr):
+    c = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+    out = np.empty_like(c)
+    lib().orc_philox_array(ctypes.c_uint64(seed), _p(c), c.shape[0], _p(out))
+    return out
 
 
 def sample_faces(seed, window, tet, w0, M, T):

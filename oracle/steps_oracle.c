@@ -609,3 +609,15 @@ int orc_step(orc_sim *s, double tau_k)
     window(s, tau_k);
     return ORC_OK;
 }
+
+/* Array forms of the building blocks, for exhaustive comparisons. */
+void orc_logf32_array(const float *x, int64_t n, float *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_logf32(x[i]);
+}
+
+void orc_philox_array(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t i = 0; i < n; ++i) orc_philox4x32_10(key, ctr + 4 * i, out + 4 * i);
+}

@@ -1,0 +1,279 @@
+"""Python binding of the C ABI in include/steps_gpu.h (argument marshalling
+only: every step of the simulation runs in the CUDA library).
+
+The functions keep the C names. Handles are opaque ctypes pointers; arrays
+are numpy arrays (host) converted to the C layout. A negative return code
+raises StepsError with the library's message. If the compiled library is
+absent this module raises on import: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsteps_gpu.so")
+
+STEPS_OCC_MEAN, STEPS_OCC_END = 1, 0
+STEPS_REORDER_NONE, STEPS_REORDER_MORTON = 0, 1
+
+ERRORS = {-1: "STEPS_ERR_ARG", -2: "STEPS_ERR_MESH", -3: "STEPS_ERR_MODEL", -4: "STEPS_ERR_OOM",
+          -5: "STEPS_ERR_CUDA", -6: "STEPS_ERR_TIMEOUT", -7: "STEPS_ERR_STATE"}
+
+# every exported symbol of include/steps_gpu.h
+EXPORTS = [
+    "steps_options_default", "steps_mesh_create", "steps_mesh_destroy", "steps_mesh_num_tets",
+    "steps_model_create", "steps_model_destroy", "steps_sim_create", "steps_sim_destroy",
+    "steps_set_counts", "steps_get_counts", "steps_set_counts_all", "steps_get_counts_all",
+    "steps_set_reac_mask", "steps_run", "steps_get_time", "steps_get_tau", "steps_get_windows",
+    "steps_last_error", "steps_debug_philox", "steps_debug_logf",
+]
+
+
+class StepsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class steps_options(ctypes.Structure):
+    _fields_ = [("occupancy", ctypes.c_int32), ("reorder", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_1610_02258_gb300.build.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "steps_options_default": (None, [ctypes.POINTER(steps_options)]),
+        "steps_mesh_create": (ctypes.c_int, [P, i64, P, i64, PP]),
+        "steps_mesh_destroy": (None, [P]),
+        "steps_mesh_num_tets": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "steps_model_create": (ctypes.c_int, [i32, P, i32, P, P, P, PP]),
+        "steps_model_destroy": (None, [P]),
+        "steps_sim_create": (ctypes.c_int, [P, P, u64, ctypes.POINTER(steps_options), P, PP]),
+        "steps_sim_destroy": (None, [P]),
+        "steps_set_counts": (ctypes.c_int, [P, i32, P]),
+        "steps_get_counts": (ctypes.c_int, [P, i32, P]),
+        "steps_set_counts_all": (ctypes.c_int, [P, P]),
+        "steps_get_counts_all": (ctypes.c_int, [P, P]),
+        "steps_set_reac_mask": (ctypes.c_int, [P, i32, P]),
+        "steps_run": (ctypes.c_int, [P, ctypes.c_double]),
+        "steps_get_time": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double)]),
+        "steps_get_tau": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double)]),
+        "steps_get_windows": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+        "steps_last_error": (ctypes.c_char_p, []),
+        "steps_debug_philox": (ctypes.c_int, [u64, P, i64, P]),
+        "steps_debug_logf": (ctypes.c_int, [P, i64, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _check(rc):
+    if rc < 0:
+        raise StepsError(rc, lib.steps_last_error().decode(errors="replace"))
+    return rc
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def steps_options_default():
+    o = steps_options()
+    lib.steps_options_default(ctypes.byref(o))
+    return o
+
+
+def steps_mesh_create(verts, tets):
+    v = np.ascontiguousarray(verts, np.float64)
+    t = np.ascontiguousarray(tets, np.int32)
+    h = ctypes.c_void_p()
+    _check(lib.steps_mesh_create(_ptr(v), v.shape[0], _ptr(t), t.shape[0], ctypes.byref(h)))
+    return h
+
+
+def steps_mesh_destroy(h):
+    lib.steps_mesh_destroy(h)
+
+
+def steps_mesh_num_tets(h):
+    n = ctypes.c_int64()
+    _check(lib.steps_mesh_num_tets(h, ctypes.byref(n)))
+    return n.value
+
+
+def steps_model_create(diff, lhs, rhs, k):
+    d = np.ascontiguousarray(diff, np.float64)
+    S = d.shape[0]
+    lh = np.ascontiguousarray(lhs, np.int32).reshape(-1, S)
+    R = lh.shape[0]
+    rh = np.ascontiguousarray(rhs, np.int32).reshape(R, S)
+    kk = np.ascontiguousarray(k, np.float64).reshape(R)
+    h = ctypes.c_void_p()
+    _check(lib.steps_model_create(S, _ptr(d), R, _ptr(lh) if R else None, _ptr(rh) if R else None,
+                                  _ptr(kk) if R else None, ctypes.byref(h)))
+    return h
+
+
+def steps_model_destroy(h):
+    lib.steps_model_destroy(h)
+
+
+def steps_sim_create(mesh, model, seed, opt=None, cuda_stream=None):
+    h = ctypes.c_void_p()
+    _check(lib.steps_sim_create(mesh, model, ctypes.c_uint64(seed), ctypes.byref(opt) if opt is not None else None,
+                                ctypes.c_void_p(cuda_stream) if cuda_stream else None, ctypes.byref(h)))
+    return h
+
+
+def steps_sim_destroy(h):
+    lib.steps_sim_destroy(h)
+
+
+def steps_set_counts(sim, species, counts):
+    c = np.ascontiguousarray(counts, np.int32)
+    _check(lib.steps_set_counts(sim, species, _ptr(c)))
+
+
+def steps_get_counts(sim, species, nt):
+    out = np.empty(nt, np.int32)
+    _check(lib.steps_get_counts(sim, species, _ptr(out)))
+    return out
+
+
+def steps_set_counts_all(sim, counts):
+    c = np.ascontiguousarray(counts, np.int32)
+    _check(lib.steps_set_counts_all(sim, _ptr(c)))
+
+
+def steps_get_counts_all(sim, n_species, nt, out=None):
+    if out is None:
+        out = np.empty((n_species, nt), np.int32)
+    _check(lib.steps_get_counts_all(sim, _ptr(out)))
+    return out
+
+
+def steps_set_reac_mask(sim, reac, active):
+    if active is None:
+        _check(lib.steps_set_reac_mask(sim, reac, None))
+    else:
+        a = np.ascontiguousarray(active, np.uint8)
+        _check(lib.steps_set_reac_mask(sim, reac, _ptr(a)))
+
+
+def steps_run(sim, t_end):
+    _check(lib.steps_run(sim, float(t_end)))
+
+
+def steps_get_time(sim):
+    t = ctypes.c_double()
+    _check(lib.steps_get_time(sim, ctypes.byref(t)))
+    return t.value
+
+
+def steps_get_tau(sim):
+    t = ctypes.c_double()
+    _check(lib.steps_get_tau(sim, ctypes.byref(t)))
+    return t.value
+
+
+def steps_get_windows(sim):
+    w, l = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib.steps_get_windows(sim, ctypes.byref(w), ctypes.byref(l)))
+    return w.value, l.value
+
+
+def steps_debug_philox(seed, ctr):
+    c = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+    out = np.empty_like(c)
+    _check(lib.steps_debug_philox(ctypes.c_uint64(seed), _ptr(c), c.shape[0], _ptr(out)))
+    return out
+
+
+def steps_debug_logf(x):
+    a = np.ascontiguousarray(x, np.float32)
+    out = np.empty_like(a)
+    _check(lib.steps_debug_logf(_ptr(a), a.size, _ptr(out)))
+    return out
+
+
+class Simulation:
+    """Owns one mesh, model and simulation handle (convenience wrapper over
+    the calls above; counts are [S, nt] numpy arrays in the caller's tet order)."""
+
+    def __init__(self, verts, tets, model, seed, occupancy=STEPS_OCC_MEAN, reorder=STEPS_REORDER_MORTON,
+                 block=256, use_graph=True, cuda_stream=None):
+        self.S = model.n_species
+        self.R = model.n_reac
+        self.nt = int(np.asarray(tets).shape[0])
+        self._mesh = steps_mesh_create(verts, tets)
+        self._model = steps_model_create(model.diff, model.lhs, model.rhs, model.k)
+        opt = steps_options_default()
+        opt.occupancy = occupancy
+        opt.reorder = reorder
+        opt.block = block
+        opt.use_graph = 1 if use_graph else 0
+        self._sim = steps_sim_create(self._mesh, self._model, seed, opt, cuda_stream)
+
+    def close(self):
+        if getattr(self, "_sim", None):
+            steps_sim_destroy(self._sim)
+            self._sim = None
+        if getattr(self, "_model", None):
+            steps_model_destroy(self._model)
+            self._model = None
+        if getattr(self, "_mesh", None):
+            steps_mesh_destroy(self._mesh)
+            self._mesh = None
+
+    def __del__(self):
+        self.close()
+
+    def set_counts(self, counts):
+        steps_set_counts_all(self._sim, counts)
+
+    def get_counts(self, out=None):
+        return steps_get_counts_all(self._sim, self.S, self.nt, out)
+
+    def set_reac_mask(self, r, mask):
+        steps_set_reac_mask(self._sim, r, mask)
+
+    def run(self, t_end):
+        steps_run(self._sim, t_end)
+
+    @property
+    def time(self):
+        return steps_get_time(self._sim)
+
+    @property
+    def tau(self):
+        return steps_get_tau(self._sim)
+
+    @property
+    def windows(self):
+        return steps_get_windows(self._sim)[0]
+
+    @property
+    def launches(self):
+        return steps_get_windows(self._sim)[1]
+
+
+def from_workload(w, occupancy=STEPS_OCC_MEAN, seed=None, **kw) -> Simulation:
+    sim = Simulation(w.verts, w.tets, w.model, w.seed if seed is None else seed, occupancy=occupancy, **kw)
+    sim.set_counts(w.counts)
+    for r, m in w.reac_masks.items():
+        sim.set_reac_mask(r, m)
+    return sim

@@ -1,0 +1,573 @@
+// C ABI of the library: mesh, model and simulation handles, the window loop
+// of Algorithm 1 on the host, and the device buffers it drives.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "steps_internal.h"
+
+using namespace steps;
+
+namespace steps {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+}  // namespace steps
+
+struct steps_mesh {
+    HostMesh m;
+};
+
+struct steps_model {
+    HostModel m;
+};
+
+namespace {
+
+constexpr int kGraphWindows = 16;  // full windows per captured graph (even: buffer parity is restored)
+
+__global__ void scatter_to_device_order(const int32_t *src, int64_t nt, int32_t S, const int32_t *inv_perm,
+                                        int32_t *dst, size_t Tpad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    const int64_t d = inv_perm ? inv_perm[i] : i;
+    for (int s = 0; s < S; ++s) dst[s * Tpad + d] = src[s * (size_t)nt + i];
+}
+
+__global__ void gather_to_original_order(const int32_t *src, int64_t nt, int32_t S, const int32_t *inv_perm,
+                                         size_t Tpad, int32_t *dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    const int64_t d = inv_perm ? inv_perm[i] : i;
+    for (int s = 0; s < S; ++s) dst[s * (size_t)nt + i] = src[s * Tpad + d];
+}
+
+__global__ void set_u64_kernel(uint64_t *p, uint64_t v) { *p = v; }
+
+bool cuda_ok(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return true;
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return false;
+}
+
+}  // namespace
+
+struct steps_sim {
+    HostModel model;
+    Tables tab;
+    steps_options opt{};
+    cudaStream_t stream = nullptr;
+    int64_t T = 0;
+    int64_t Tpad = 0;
+    int S = 0;
+    uint64_t seed = 0;
+    // device state
+    int32_t *d_cnt[2] = {nullptr, nullptr};
+    int cur = 0;
+    int4 *d_nbr = nullptr;
+    uint4 *d_thr = nullptr;
+    float *d_inv_nav = nullptr;
+    int32_t *d_orig = nullptr;      // device index -> original id (null without reordering)
+    int32_t *d_inv_perm = nullptr;  // original id -> device index (null without reordering)
+    uint32_t *d_rmask = nullptr;
+    std::vector<uint32_t> h_rmask;  // device order
+    uint32_t *d_err = nullptr;
+    uint64_t *d_window_base = nullptr;
+    int32_t *d_stage = nullptr;     // [S * nt] original-order staging
+    // time
+    double t_base = 0.0;
+    int64_t k_grid = 0;
+    uint64_t k_total = 0;
+    uint64_t launches = 0;
+    uint32_t scale_full[kMaxSpecies] = {};
+    // graphs of kGraphWindows full windows, one per starting buffer
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+    double time() const { return k_grid == 0 ? t_base : t_base + (double)k_grid * tab.tau; }
+
+    ~steps_sim() {
+        for (auto &g : graph)
+            if (g) cudaGraphExecDestroy(g);
+        cudaFree(d_cnt[0]);
+        cudaFree(d_cnt[1]);
+        cudaFree(d_nbr);
+        cudaFree(d_thr);
+        cudaFree(d_inv_nav);
+        cudaFree(d_orig);
+        cudaFree(d_inv_perm);
+        cudaFree(d_rmask);
+        cudaFree(d_err);
+        cudaFree(d_window_base);
+        cudaFree(d_stage);
+    }
+
+    void drop_graphs() {
+        for (auto &g : graph) {
+            if (g) cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    }
+
+    StepArgs args(int from, uint64_t window, const uint64_t *base, double tau_k, const uint32_t *scale) const {
+        StepArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.cur = d_cnt[from];
+        a.nxt = d_cnt[1 - from];
+        a.nbr = d_nbr;
+        a.thr = d_thr;
+        a.inv_nav = d_inv_nav;
+        a.orig = d_orig;
+        a.rmask = d_rmask;
+        a.err = d_err;
+        a.T = (int32_t)T;
+        a.Tpad = (int32_t)Tpad;
+        a.key0 = (uint32_t)seed;
+        a.key1 = (uint32_t)(seed >> 32);
+        a.window = window;
+        a.window_base = base;
+        a.tau_k = tau_k;
+        a.inv_tau_k = 1.0 / tau_k;
+        a.tau_dn = (float)tau_k;
+        if ((double)a.tau_dn > tau_k) a.tau_dn = std::nextafter(a.tau_dn, 0.0f);
+        a.occ = opt.occupancy;
+        std::memcpy(a.scale, scale, sizeof(a.scale));
+        return a;
+    }
+
+    int window_launch(double tau_k) {  // one window of explicit length, plain launch
+        uint32_t scale[kMaxSpecies] = {};
+        for (int s = 0; s < S; ++s) scale[s] = species_scale(model, tab, s, tau_k);
+        StepArgs a = args(cur, k_total, nullptr, tau_k, scale);
+        int rc = launch_step(model.dev, a, opt.block, stream);
+        if (rc) return rc;
+        ++launches;
+        cur = 1 - cur;
+        ++k_total;
+        return STEPS_OK;
+    }
+
+    int capture_graph(int from) {
+        cudaStream_t cs = nullptr;
+        if (!cuda_ok(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate")) return STEPS_ERR_CUDA;
+        int rc = STEPS_OK;
+        cudaGraph_t g = nullptr;
+        if (!cuda_ok(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture")) {
+            cudaStreamDestroy(cs);
+            return STEPS_ERR_CUDA;
+        }
+        int b = from;
+        for (int q = 0; q < kGraphWindows && rc == STEPS_OK; ++q) {
+            StepArgs a = args(b, (uint64_t)q, d_window_base, tab.tau, scale_full);
+            rc = launch_step(model.dev, a, opt.block, cs);
+            b = 1 - b;
+        }
+        if (rc == STEPS_OK) rc = launch_add_u64(d_window_base, kGraphWindows, cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (rc == STEPS_OK && !cuda_ok(e, "cudaStreamEndCapture")) rc = STEPS_ERR_CUDA;
+        if (rc == STEPS_OK && !cuda_ok(cudaGraphInstantiate(&graph[from], g, 0), "cudaGraphInstantiate"))
+            rc = STEPS_ERR_CUDA;
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        return rc;
+    }
+
+    int full_windows(int64_t n) {
+        int64_t done = 0;
+        if (opt.use_graph && n >= kGraphWindows) {
+            if (!graph[cur]) {
+                int rc = capture_graph(cur);
+                if (rc) return rc;
+            }
+            set_u64_kernel<<<1, 1, 0, stream>>>(d_window_base, k_total);
+            if (!cuda_ok(cudaGetLastError(), "set window base")) return STEPS_ERR_CUDA;
+            ++launches;
+            while (n - done >= kGraphWindows) {
+                if (!cuda_ok(cudaGraphLaunch(graph[cur], stream), "cudaGraphLaunch")) return STEPS_ERR_CUDA;
+                launches += kGraphWindows + 1;
+                done += kGraphWindows;
+                k_total += kGraphWindows;  // even: cur unchanged
+            }
+        }
+        for (; done < n; ++done) {
+            StepArgs a = args(cur, k_total, nullptr, tab.tau, scale_full);
+            int rc = launch_step(model.dev, a, opt.block, stream);
+            if (rc) return rc;
+            ++launches;
+            cur = 1 - cur;
+            ++k_total;
+        }
+        return STEPS_OK;
+    }
+};
+
+#define CHECK_NULL(p, name)                                    \
+    do {                                                       \
+        if (!(p)) {                                            \
+            set_error(std::string(name) + ": NULL argument");  \
+            return STEPS_ERR_ARG;                              \
+        }                                                      \
+    } while (0)
+
+extern "C" {
+
+const char *steps_last_error(void) { return g_last_error.c_str(); }
+
+void steps_options_default(steps_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->occupancy = STEPS_OCC_MEAN;
+    opt->reorder = STEPS_REORDER_MORTON;
+    opt->block = 256;
+    opt->use_graph = 1;
+}
+
+int steps_mesh_create(const double *verts_xyz, int64_t nv, const int32_t *tets, int64_t nt, steps_mesh **out) {
+    CHECK_NULL(out, "steps_mesh_create");
+    *out = nullptr;
+    std::unique_ptr<steps_mesh> m(new (std::nothrow) steps_mesh);
+    if (!m) {
+        set_error("steps_mesh_create: out of host memory");
+        return STEPS_ERR_OOM;
+    }
+    int rc;
+    try {
+        rc = build_mesh(verts_xyz, nv, tets, nt, m->m);
+    } catch (const std::bad_alloc &) {
+        set_error("steps_mesh_create: out of host memory");
+        return STEPS_ERR_OOM;
+    }
+    if (rc) return rc;
+    *out = m.release();
+    return STEPS_OK;
+}
+
+void steps_mesh_destroy(steps_mesh *mesh) { delete mesh; }
+
+int steps_mesh_num_tets(const steps_mesh *mesh, int64_t *nt) {
+    CHECK_NULL(mesh, "steps_mesh_num_tets");
+    CHECK_NULL(nt, "steps_mesh_num_tets");
+    *nt = mesh->m.nt;
+    return STEPS_OK;
+}
+
+int steps_model_create(int32_t n_species, const double *diff, int32_t n_reac, const int32_t *lhs,
+                       const int32_t *rhs, const double *k, steps_model **out) {
+    CHECK_NULL(out, "steps_model_create");
+    *out = nullptr;
+    std::unique_ptr<steps_model> m(new (std::nothrow) steps_model);
+    if (!m) {
+        set_error("steps_model_create: out of host memory");
+        return STEPS_ERR_OOM;
+    }
+    int rc = build_model(n_species, diff, n_reac, lhs, rhs, k, m->m);
+    if (rc) return rc;
+    *out = m.release();
+    return STEPS_OK;
+}
+
+void steps_model_destroy(steps_model *model) { delete model; }
+
+int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t seed, const steps_options *opt,
+                     void *cuda_stream, steps_sim **out) {
+    CHECK_NULL(out, "steps_sim_create");
+    *out = nullptr;
+    CHECK_NULL(mesh, "steps_sim_create");
+    CHECK_NULL(model, "steps_sim_create");
+    std::unique_ptr<steps_sim> s(new (std::nothrow) steps_sim);
+    if (!s) {
+        set_error("steps_sim_create: out of host memory");
+        return STEPS_ERR_OOM;
+    }
+    if (opt) {
+        s->opt = *opt;
+        if (s->opt.block == 0) s->opt.block = 256;
+        if (s->opt.block != 64 && s->opt.block != 128 && s->opt.block != 256 && s->opt.block != 512) {
+            set_error("steps_sim_create: block must be 64, 128, 256 or 512");
+            return STEPS_ERR_ARG;
+        }
+        if (s->opt.occupancy != STEPS_OCC_MEAN && s->opt.occupancy != STEPS_OCC_END) {
+            set_error("steps_sim_create: bad occupancy mode");
+            return STEPS_ERR_ARG;
+        }
+    } else {
+        steps_options_default(&s->opt);
+    }
+    s->model = model->m;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->T = mesh->m.nt;
+    s->Tpad = (s->T + 31) / 32 * 32;
+    s->S = s->model.S;
+    s->seed = seed;
+    try {
+        build_tables(mesh->m, s->model, s->opt.reorder, s->tab);
+    } catch (const std::bad_alloc &) {
+        set_error("steps_sim_create: out of host memory");
+        return STEPS_ERR_OOM;
+    }
+    for (int sp = 0; sp < s->S; ++sp) s->scale_full[sp] = species_scale(s->model, s->tab, sp, s->tab.tau);
+
+    const size_t T = (size_t)s->T, Tpad = (size_t)s->Tpad, S = (size_t)s->S;
+    bool reordered = false;
+    for (size_t d = 0; d < T && !reordered; ++d) reordered = s->tab.perm[d] != (int32_t)d;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    alloc((void **)&s->d_cnt[0], S * Tpad * 4);
+    alloc((void **)&s->d_cnt[1], S * Tpad * 4);
+    // per-tet tables are padded to Tpad entries (zeros) so that the step
+    // kernel's bulk copies of a block's tile are whole multiples of 16 bytes
+    alloc((void **)&s->d_nbr, Tpad * 16);
+    alloc((void **)&s->d_thr, Tpad * 16);
+    alloc((void **)&s->d_inv_nav, Tpad * 4);
+    alloc((void **)&s->d_err, 4);
+    alloc((void **)&s->d_window_base, 8);
+    alloc((void **)&s->d_stage, S * T * 4);
+    if (reordered) {
+        alloc((void **)&s->d_orig, Tpad * 4);
+        alloc((void **)&s->d_inv_perm, T * 4);
+    }
+    if (e != cudaSuccess) {
+        set_error(std::string("steps_sim_create: device allocation failed: ") + cudaGetErrorString(e));
+        cudaGetLastError();
+        return STEPS_ERR_OOM;
+    }
+    bool ok = cuda_ok(cudaMemset(s->d_nbr, 0xFF, Tpad * 16), "memset") &&
+              cuda_ok(cudaMemset(s->d_thr, 0, Tpad * 16), "memset") &&
+              cuda_ok(cudaMemset(s->d_inv_nav, 0, Tpad * 4), "memset") &&
+              cuda_ok(cudaMemcpy(s->d_nbr, s->tab.nbr_dev.data(), T * 16, cudaMemcpyHostToDevice), "upload nbr") &&
+              cuda_ok(cudaMemcpy(s->d_thr, s->tab.thr_dev.data(), T * 16, cudaMemcpyHostToDevice), "upload thr") &&
+              cuda_ok(cudaMemcpy(s->d_inv_nav, s->tab.inv_nav_dev.data(), T * 4, cudaMemcpyHostToDevice),
+                      "upload inv_nav") &&
+              cuda_ok(cudaMemset(s->d_cnt[0], 0, S * Tpad * 4), "memset") &&
+              cuda_ok(cudaMemset(s->d_cnt[1], 0, S * Tpad * 4), "memset") &&
+              cuda_ok(cudaMemset(s->d_err, 0, 4), "memset") && cuda_ok(cudaMemset(s->d_window_base, 0, 8), "memset");
+    if (ok && reordered)
+        ok = cuda_ok(cudaMemset(s->d_orig, 0, Tpad * 4), "memset") &&
+             cuda_ok(cudaMemcpy(s->d_orig, s->tab.perm.data(), T * 4, cudaMemcpyHostToDevice), "upload perm") &&
+             cuda_ok(cudaMemcpy(s->d_inv_perm, s->tab.inv_perm.data(), T * 4, cudaMemcpyHostToDevice),
+                     "upload inv_perm");
+    if (!ok) return STEPS_ERR_CUDA;
+    *out = s.release();
+    return STEPS_OK;
+}
+
+void steps_sim_destroy(steps_sim *sim) {
+    if (!sim) return;
+    if (sim->stream) cudaStreamSynchronize(sim->stream);
+    else cudaDeviceSynchronize();
+    delete sim;
+}
+
+static int put_counts(steps_sim *sim, int32_t s0, int32_t ns, const int32_t *counts) {
+    const size_t T = (size_t)sim->T, Tpad = (size_t)sim->Tpad;
+    if (!cuda_ok(cudaMemcpyAsync(sim->d_stage, counts, (size_t)ns * T * 4, cudaMemcpyHostToDevice, sim->stream),
+                 "steps_set_counts: copy"))
+        return STEPS_ERR_CUDA;
+    scatter_to_device_order<<<(unsigned)((T + 255) / 256), 256, 0, sim->stream>>>(
+        sim->d_stage, (int64_t)T, ns, sim->d_inv_perm, sim->d_cnt[sim->cur] + (size_t)s0 * Tpad, Tpad);
+    if (!cuda_ok(cudaGetLastError(), "steps_set_counts: scatter")) return STEPS_ERR_CUDA;
+    // the receiving buffer of mobile species must start at zero
+    if (!cuda_ok(cudaMemsetAsync(sim->d_cnt[1 - sim->cur] + (size_t)s0 * Tpad, 0, (size_t)ns * Tpad * 4,
+                                 sim->stream),
+                 "steps_set_counts: memset"))
+        return STEPS_ERR_CUDA;
+    if (!cuda_ok(cudaStreamSynchronize(sim->stream), "steps_set_counts")) return STEPS_ERR_CUDA;
+    return STEPS_OK;
+}
+
+static int check_counts(const int32_t *c, size_t n, const char *who) {
+    for (size_t i = 0; i < n; ++i)
+        if (c[i] < 0) {
+            set_error(std::string(who) + ": negative count");
+            return STEPS_ERR_ARG;
+        }
+    return STEPS_OK;
+}
+
+int steps_set_counts(steps_sim *sim, int32_t species, const int32_t *counts) {
+    CHECK_NULL(sim, "steps_set_counts");
+    CHECK_NULL(counts, "steps_set_counts");
+    if (species < 0 || species >= sim->S) {
+        set_error("steps_set_counts: species out of range");
+        return STEPS_ERR_ARG;
+    }
+    int rc = check_counts(counts, (size_t)sim->T, "steps_set_counts");
+    return rc ? rc : put_counts(sim, species, 1, counts);
+}
+
+int steps_set_counts_all(steps_sim *sim, const int32_t *counts) {
+    CHECK_NULL(sim, "steps_set_counts_all");
+    CHECK_NULL(counts, "steps_set_counts_all");
+    int rc = check_counts(counts, (size_t)sim->T * sim->S, "steps_set_counts_all");
+    return rc ? rc : put_counts(sim, 0, sim->S, counts);
+}
+
+static int fetch_counts(const steps_sim *sim, int32_t s0, int32_t ns, int32_t *out) {
+    const size_t T = (size_t)sim->T, Tpad = (size_t)sim->Tpad;
+    gather_to_original_order<<<(unsigned)((T + 255) / 256), 256, 0, sim->stream>>>(
+        sim->d_cnt[sim->cur] + (size_t)s0 * Tpad, (int64_t)T, ns, sim->d_inv_perm, Tpad, sim->d_stage);
+    if (!cuda_ok(cudaGetLastError(), "steps_get_counts: gather")) return STEPS_ERR_CUDA;
+    if (!cuda_ok(cudaMemcpyAsync(out, sim->d_stage, (size_t)ns * T * 4, cudaMemcpyDeviceToHost, sim->stream),
+                 "steps_get_counts: copy"))
+        return STEPS_ERR_CUDA;
+    if (!cuda_ok(cudaStreamSynchronize(sim->stream), "steps_get_counts")) return STEPS_ERR_CUDA;
+    return STEPS_OK;
+}
+
+int steps_get_counts(const steps_sim *sim, int32_t species, int32_t *out) {
+    CHECK_NULL(sim, "steps_get_counts");
+    CHECK_NULL(out, "steps_get_counts");
+    if (species < 0 || species >= sim->S) {
+        set_error("steps_get_counts: species out of range");
+        return STEPS_ERR_ARG;
+    }
+    return fetch_counts(sim, species, 1, out);
+}
+
+int steps_get_counts_all(const steps_sim *sim, int32_t *out) {
+    CHECK_NULL(sim, "steps_get_counts_all");
+    CHECK_NULL(out, "steps_get_counts_all");
+    return fetch_counts(sim, 0, sim->S, out);
+}
+
+int steps_set_reac_mask(steps_sim *sim, int32_t reac, const uint8_t *active) {
+    CHECK_NULL(sim, "steps_set_reac_mask");
+    if (reac < 0 || reac >= sim->model.R) {
+        set_error("steps_set_reac_mask: reaction out of range");
+        return STEPS_ERR_ARG;
+    }
+    const size_t T = (size_t)sim->T;
+    if (sim->h_rmask.empty()) sim->h_rmask.assign(T, 0xFFFFFFFFu);
+    const uint32_t bit = 1u << reac;
+    for (size_t d = 0; d < T; ++d) {
+        const bool on = !active || active[sim->tab.perm[d]] != 0;
+        sim->h_rmask[d] = on ? (sim->h_rmask[d] | bit) : (sim->h_rmask[d] & ~bit);
+    }
+    if (!sim->d_rmask) {
+        if (!cuda_ok(cudaMalloc((void **)&sim->d_rmask, (size_t)sim->Tpad * 4), "steps_set_reac_mask: alloc") ||
+            !cuda_ok(cudaMemset(sim->d_rmask, 0, (size_t)sim->Tpad * 4), "steps_set_reac_mask: memset"))
+            return STEPS_ERR_OOM;
+        sim->drop_graphs();  // kernel arguments change
+    }
+    if (!cuda_ok(cudaStreamSynchronize(sim->stream), "steps_set_reac_mask") ||
+        !cuda_ok(cudaMemcpy(sim->d_rmask, sim->h_rmask.data(), T * 4, cudaMemcpyHostToDevice),
+                 "steps_set_reac_mask: copy"))
+        return STEPS_ERR_CUDA;
+    return STEPS_OK;
+}
+
+int steps_run(steps_sim *sim, double t_end) {
+    CHECK_NULL(sim, "steps_run");
+    if (!std::isfinite(t_end)) {
+        set_error("steps_run: t_end must be finite");
+        return STEPS_ERR_ARG;
+    }
+    const double tau = sim->tab.tau;
+    const bool finite = std::isfinite(tau);
+    const double tol = finite ? 1e-9 * tau : 0.0;
+    for (;;) {
+        const double t = sim->time();
+        if (!(t_end - t > tol)) break;
+        if (finite && t + tau <= t_end + tol) {
+            // the consecutive full windows the loop of Algorithm 1 takes from here
+            int64_t n = 0;
+            while (n < kWindowBatch) {
+                const int64_t k = sim->k_grid + n;
+                const double tt = k == 0 ? sim->t_base : sim->t_base + (double)k * tau;
+                if (!(t_end - tt > tol) || !(tt + tau <= t_end + tol)) break;
+                ++n;
+            }
+            int rc = sim->full_windows(n);
+            if (rc) return rc;
+            sim->k_grid += n;
+        } else {
+            int rc = sim->window_launch(t_end - t);  // shortened last window (Algorithm 1)
+            if (rc) return rc;
+            sim->t_base = t_end;
+            sim->k_grid = 0;
+            break;
+        }
+    }
+    uint32_t err = 0;
+    if (!cuda_ok(cudaMemcpyAsync(&err, sim->d_err, 4, cudaMemcpyDeviceToHost, sim->stream), "steps_run: error word") ||
+        !cuda_ok(cudaStreamSynchronize(sim->stream), "steps_run"))
+        return STEPS_ERR_CUDA;
+    if (err) {
+        cudaMemsetAsync(sim->d_err, 0, 4, sim->stream);
+        if (err & 4u) {
+            set_error("steps_run: a bulk copy into shared memory did not complete within its wait limit");
+            return STEPS_ERR_TIMEOUT;
+        }
+        set_error(err & 2u ? "steps_run: a tet fired more than 2^24 reactions in one window (rates too large)"
+                           : "steps_run: a negative count was seen on the device");
+        return STEPS_ERR_STATE;
+    }
+    return STEPS_OK;
+}
+
+int steps_get_time(const steps_sim *sim, double *t) {
+    CHECK_NULL(sim, "steps_get_time");
+    CHECK_NULL(t, "steps_get_time");
+    *t = sim->time();
+    return STEPS_OK;
+}
+
+int steps_get_tau(const steps_sim *sim, double *tau) {
+    CHECK_NULL(sim, "steps_get_tau");
+    CHECK_NULL(tau, "steps_get_tau");
+    *tau = sim->tab.tau;
+    return STEPS_OK;
+}
+
+int steps_get_windows(const steps_sim *sim, uint64_t *windows, uint64_t *launches) {
+    CHECK_NULL(sim, "steps_get_windows");
+    if (windows) *windows = sim->k_total;
+    if (launches) *launches = sim->launches;
+    return STEPS_OK;
+}
+
+int steps_debug_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out) {
+    CHECK_NULL(ctr, "steps_debug_philox");
+    CHECK_NULL(out, "steps_debug_philox");
+    if (n < 0) return STEPS_ERR_ARG;
+    if (n == 0) return STEPS_OK;
+    uint32_t *dc = nullptr, *dout = nullptr;
+    int rc = STEPS_OK;
+    if (!cuda_ok(cudaMalloc((void **)&dc, (size_t)n * 16), "alloc") ||
+        !cuda_ok(cudaMalloc((void **)&dout, (size_t)n * 16), "alloc"))
+        rc = STEPS_ERR_OOM;
+    if (!rc && !cuda_ok(cudaMemcpy(dc, ctr, (size_t)n * 16, cudaMemcpyHostToDevice), "copy")) rc = STEPS_ERR_CUDA;
+    if (!rc) rc = launch_philox_test(seed, dc, n, dout, nullptr);
+    if (!rc && !cuda_ok(cudaMemcpy(out, dout, (size_t)n * 16, cudaMemcpyDeviceToHost), "copy")) rc = STEPS_ERR_CUDA;
+    cudaFree(dc);
+    cudaFree(dout);
+    return rc;
+}
+
+int steps_debug_logf(const float *x, int64_t n, float *out) {
+    CHECK_NULL(x, "steps_debug_logf");
+    CHECK_NULL(out, "steps_debug_logf");
+    if (n < 0) return STEPS_ERR_ARG;
+    if (n == 0) return STEPS_OK;
+    float *dx = nullptr, *dout = nullptr;
+    int rc = STEPS_OK;
+    if (!cuda_ok(cudaMalloc((void **)&dx, (size_t)n * 4), "alloc") ||
+        !cuda_ok(cudaMalloc((void **)&dout, (size_t)n * 4), "alloc"))
+        rc = STEPS_ERR_OOM;
+    if (!rc && !cuda_ok(cudaMemcpy(dx, x, (size_t)n * 4, cudaMemcpyHostToDevice), "copy")) rc = STEPS_ERR_CUDA;
+    if (!rc) rc = launch_logf_test(dx, n, dout, nullptr);
+    if (!rc && !cuda_ok(cudaMemcpy(out, dout, (size_t)n * 4, cudaMemcpyDeviceToHost), "copy")) rc = STEPS_ERR_CUDA;
+    cudaFree(dx);
+    cudaFree(dout);
+    return rc;
+}
+
+}  // extern "C"

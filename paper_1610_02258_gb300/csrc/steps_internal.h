@@ -1,0 +1,111 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <vector_types.h>
+
+#include "../../include/steps_gpu.h"
+
+namespace steps {
+
+constexpr int kMaxSpecies = STEPS_MAX_SPECIES;
+constexpr int kMaxReac = STEPS_MAX_REACTIONS;
+constexpr int kMaxChanges = 6;
+constexpr double kAvogadro = 6.02214076e23;
+// Reaction events one tet may fire in one window before the kernel gives up
+// on it and raises error bit 2 (a guard against runaway rate constants).
+constexpr uint32_t kMaxEventsPerWindow = 1u << 24;
+// Full windows counted and enqueued per batch by steps_run.
+constexpr int64_t kWindowBatch = 1 << 16;
+
+// Stream purposes of the counter-based generator (top 4 bits of counter word 3).
+constexpr uint32_t kPurposeReac = 1;
+constexpr uint32_t kPurposeRound = 2;
+constexpr uint32_t kPurposeDiff = 3;
+
+// Reaction kinds by propensity form.
+enum ReacType : int8_t { kOrder0 = 0, kOrder1 = 1, kOrder2 = 2, kDimer = 3 };
+
+void set_error(const std::string &msg);
+
+// ---------------------------------------------------------------- device-side model
+struct ReacDesc {
+    float k;                      // rate constant, float
+    int8_t type;                  // ReacType
+    int8_t ra, rb;                // reactant species (lower index first), -1 = none
+    int8_t nchg;                  // species changed (delta != 0), increasing species order
+    int8_t chg_s[kMaxChanges];
+    int8_t chg_d[kMaxChanges];
+};
+
+struct ModelDev {
+    int32_t S, R;
+    uint32_t diffusive;           // bit s set when D_s > 0
+    ReacDesc reac[kMaxReac];
+};
+
+// Arguments of one diffusion window.
+struct StepArgs {
+    int32_t *cur;                 // [S][Tpad] counts at window start; mobile entries are zeroed as read
+    int32_t *nxt;                 // [S][Tpad] counts at window end (mobile entries must be zero on entry)
+    const int4 *nbr;              // [T] face neighbours (device index), -1 = boundary
+    const uint4 *thr;             // [T] cumulative face thresholds at the full window, 2^31 fixed point
+    const float *inv_nav;         // [T] 1 / (N_A V_L) as float
+    const int32_t *orig;          // [T] original tet id (RNG key), or nullptr for identity
+    const uint32_t *rmask;        // [T] active-reaction bits, or nullptr = all active
+    uint32_t *err;                // device error word
+    int32_t T, Tpad;
+    uint32_t key0, key1;          // Philox key = seed
+    uint64_t window;              // window index of this launch (RNG counter)
+    const uint64_t *window_base;  // if set, window = *window_base + window (graph replay)
+    double tau_k, inv_tau_k;
+    float tau_dn;                 // largest float <= tau_k
+    int32_t occ;                  // STEPS_OCC_*
+    uint32_t scale[kMaxSpecies];  // per-species fixed-point scale for this window length
+};
+
+// ---------------------------------------------------------------- host objects
+struct HostMesh {
+    int64_t nv = 0, nt = 0;
+    std::vector<double> verts;    // [nv*3]
+    std::vector<int32_t> tets;    // [nt*4]
+    std::vector<int32_t> nbr;     // [nt*4] original order, -1 boundary
+    std::vector<double> vol;      // [nt] m^3
+    std::vector<double> g;        // [nt*4] A/(V d), 0 on boundary
+    std::vector<double> bary;     // [nt*3]
+};
+
+struct HostModel {
+    int32_t S = 0, R = 0;
+    std::vector<double> D;        // [S]
+    std::vector<int32_t> lhs, rhs;  // [R*S]
+    std::vector<double> k;        // [R]
+    ModelDev dev{};
+};
+
+// steps_host.cpp
+int build_mesh(const double *verts, int64_t nv, const int32_t *tets, int64_t nt, HostMesh &m);
+int build_model(int32_t S, const double *D, int32_t R, const int32_t *lhs, const int32_t *rhs,
+                const double *k, HostModel &m);
+
+struct Tables {
+    double tau = 0, dmax = 0, gmax = 0;
+    std::vector<int32_t> perm;      // device index -> original id
+    std::vector<int32_t> inv_perm;  // original id -> device index
+    std::vector<int32_t> nbr_dev;   // [T*4] device order, device indices
+    std::vector<uint32_t> thr_dev;  // [T*4] device order
+    std::vector<float> inv_nav_dev; // [T]
+};
+void build_tables(const HostMesh &mesh, const HostModel &model, int reorder, Tables &t);
+uint32_t species_scale(const HostModel &model, const Tables &t, int s, double tau_k);
+
+// steps_kernels.cu
+int launch_step(const ModelDev &m, const StepArgs &a, int block, void *stream);
+int launch_philox_test(uint64_t seed, const uint32_t *d_ctr, int64_t n, uint32_t *d_out, void *stream);
+int launch_logf_test(const float *d_x, int64_t n, float *d_out, void *stream);
+int launch_add_u64(uint64_t *p, uint64_t v, void *stream);
+
+}  // namespace steps

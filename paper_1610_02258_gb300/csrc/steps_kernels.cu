@@ -1,0 +1,525 @@
+// Device code of the operator-split step (Parallel STEPS, Algorithm 1):
+// one fused kernel per diffusion window runs, for every tet, the reaction
+// SSA operator and then the diffusion operator, scattering leaving molecules
+// into the next count buffer.
+//
+// Compiled with -fmad=false: every floating-point operation that decides an
+// integer (a reaction time, a reaction choice, a rounded trial count) is a
+// single IEEE operation in the order written, so the same formulas evaluated
+// on a host give the same bits.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "steps_internal.h"
+
+namespace steps {
+
+namespace {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two
+// 32x32->64 multiplies with the Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
+                                               uint32_t c2, uint32_t c3) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c0 = n0;
+        c1 = (uint32_t)p1;
+        c2 = n2;
+        c3 = (uint32_t)p0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &b, uint32_t k) {
+    return k == 0 ? b.x : k == 1 ? b.y : k == 2 ? b.z : b.w;
+}
+
+// ---- TMA (bulk async copy) global -> shared, completed on an mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bytes: multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase with the given parity to complete, for at most about
+// 2^30 clock cycles (~0.5 s); returns false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1ll << 30)) return false;
+    }
+    return true;
+}
+
+// Natural log in single precision from the atanh series:
+// x = 2^e f, f in (sqrt(1/2), sqrt(2)]; ln f = 2 atanh(s), s = (f-1)/(f+1),
+// summed to s^11; e*ln2 added as a high part (exact for |e| < 2^8) and a low part.
+__device__ __forceinline__ float steps_logf(float x) {
+    const uint32_t u = __float_as_uint(x);
+    int e = (int)((u >> 23) & 0xffu) - 127;
+    float f = __uint_as_float((u & 0x007fffffu) | 0x3f800000u);
+    if (f > 1.41421356f) {
+        f = __fmul_rn(f, 0.5f);
+        e = e + 1;
+    }
+    const float s = __fdiv_rn(__fsub_rn(f, 1.0f), __fadd_rn(f, 1.0f));
+    const float z = __fmul_rn(s, s);
+    float p = 0.0909090909f;
+    p = __fadd_rn(__fmul_rn(p, z), 0.111111111f);
+    p = __fadd_rn(__fmul_rn(p, z), 0.142857143f);
+    p = __fadd_rn(__fmul_rn(p, z), 0.2f);
+    p = __fadd_rn(__fmul_rn(p, z), 0.333333333f);
+    p = __fadd_rn(__fmul_rn(p, z), 1.0f);
+    const float lnf = __fmul_rn(__fadd_rn(s, s), p);
+    const float fe = __int2float_rn(e);
+    const float lo = __fadd_rn(__fmul_rn(fe, 1.42860682e-06f), lnf);
+    return __fadd_rn(__fmul_rn(fe, 0.693145752f), lo);
+}
+
+// Uniform in (0, 1]: ((w >> 8) + 1) * 2^-24, exact in float.
+__device__ __forceinline__ float unit24f(uint32_t w) {
+    return __fmul_rn(__uint2float_rn((w >> 8) + 1u), 5.9604644775390625e-08f);
+}
+
+// Mass-action propensity in float (order 0: k N_A V; 1: k N; 2: k/(N_A V) N_a N_b;
+// dimer: k/(N_A V) N (N-1)).
+__device__ __forceinline__ float propensity(const ReacDesc &d, const int32_t *cnt, int stride, float inv_nav) {
+    switch (d.type) {
+    case kOrder0:
+        return __fdiv_rn(d.k, inv_nav);
+    case kOrder1:
+        return __fmul_rn(d.k, __int2float_rn(cnt[d.ra * stride]));
+    case kOrder2: {
+        const float c = __fmul_rn(d.k, inv_nav);
+        return __fmul_rn(__fmul_rn(c, __int2float_rn(cnt[d.ra * stride])), __int2float_rn(cnt[d.rb * stride]));
+    }
+    default: {
+        const float c = __fmul_rn(d.k, inv_nav);
+        const int32_t n = cnt[d.ra * stride];
+        return __fmul_rn(__fmul_rn(c, __int2float_rn(n)), __int2float_rn(n - 1));
+    }
+    }
+}
+
+// Reaction SSA operator for one tet over tau_k (Algorithm 1, reaction part):
+// Gillespie's direct method with float propensities and double time, and
+// the time-weighted occupancy of every species a fired reaction changes.
+// Counts live in shared memory (cnt[s * BLOCK]); on return trial[s * BLOCK]
+// holds the integer trial count of every diffusive species the reactions
+// changed (mean occupancy, stochastically rounded, clamped to the end count;
+// or the end count in END mode). Returns error bits.
+template <int BLOCK>
+__device__ uint32_t ssa_tet(const ModelDev &m, const StepArgs &a, int32_t *cnt, int32_t *trial, uint32_t tet,
+                            uint32_t c0, uint32_t c3, float inv_nav, uint32_t active) {
+    uint32_t touched = 0, bad = 0;
+    double O[kMaxSpecies], tS[kMaxSpecies];
+    double dt_acc = 0.0;
+    uint32_t j = 0;
+    for (;;) {
+        float ar[kMaxReac];
+        float a0 = 0.0f;
+#pragma unroll
+        for (int r = 0; r < kMaxReac; ++r) {
+            ar[r] = 0.0f;
+            if (r < m.R) {
+                if ((active >> r) & 1u) ar[r] = propensity(m.reac[r], cnt, BLOCK, inv_nav);
+                a0 = __fadd_rn(a0, ar[r]);
+            }
+        }
+        if (!(a0 > 0.0f)) break;
+        if (j >= kMaxEventsPerWindow) {  // pathological rates: stop and report, never spin
+            bad |= 2u;
+            break;
+        }
+        const uint4 w = philox4x32_10(a.key0, a.key1, c0, tet, j++, (kPurposeReac << 28) | c3);
+        const float dt = __fdiv_rn(-steps_logf(unit24f(w.x)), a0);
+        const double dt_new = __dadd_rn(dt_acc, (double)dt);
+        if (dt_new > a.tau_k) break;
+        const float target = __fmul_rn(unit24f(w.y), a0);
+        float c = 0.0f;
+        int pick = -1;
+#pragma unroll
+        for (int r = 0; r < kMaxReac; ++r) {
+            if (r < m.R && pick < 0) {
+                c = __fadd_rn(c, ar[r]);
+                if (c > target) pick = r;
+            }
+        }
+        if (pick < 0) {
+#pragma unroll
+            for (int r = kMaxReac - 1; r >= 0; --r)
+                if (r < m.R && pick < 0 && ar[r] > 0.0f) pick = r;
+        }
+        if (pick < 0) break;
+        dt_acc = dt_new;
+        const ReacDesc &d = m.reac[pick];
+        for (int q = 0; q < d.nchg; ++q) {
+            const int s = d.chg_s[q];
+            const int32_t n = cnt[s * BLOCK];
+            const bool seen = (touched >> s) & 1u;
+            const double o = seen ? O[s] : 0.0;
+            const double ts = seen ? tS[s] : 0.0;
+            O[s] = __dadd_rn(o, __dmul_rn((double)n, __dsub_rn(dt_acc, ts)));
+            tS[s] = dt_acc;
+            touched |= 1u << s;
+            cnt[s * BLOCK] = n + d.chg_d[q];
+        }
+    }
+    // trial counts of the changed diffusive species, one set bit at a time
+    uint32_t todo = touched & m.diffusive;
+    uint32_t rblk = 0xFFFFFFFFu;
+    uint4 rb = make_uint4(0, 0, 0, 0);
+    while (todo) {
+        const int s = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int32_t N = cnt[s * BLOCK];
+        int32_t M = N;
+        if (a.occ) {
+            // Nbar = (O_S + N_S (tau - t_S)) / tau, stochastically rounded, clamped to N_S
+            const double occ = __dadd_rn(O[s], __dmul_rn((double)N, __dsub_rn(a.tau_k, tS[s])));
+            const double nbar = __dmul_rn(occ, a.inv_tau_k);
+            const double fl = floor(nbar);
+            const double frac = __dsub_rn(nbar, fl);
+            if ((uint32_t)(s >> 2) != rblk) {
+                rblk = (uint32_t)(s >> 2);
+                rb = philox4x32_10(a.key0, a.key1, c0, tet, rblk, (kPurposeRound << 28) | c3);
+            }
+            const double u = __dmul_rn(__dadd_rn((double)word_of(rb, s & 3), 0.5), 2.3283064365386963e-10);
+            long long mm = (long long)fl + (u < frac ? 1 : 0);
+            mm = mm < 0 ? 0 : mm;
+            M = mm > N ? N : (int32_t)mm;
+        }
+        trial[s * BLOCK] = M;
+    }
+    return bad;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the total.
+template <int BLOCK>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *out, uint32_t *warp_tot) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = lane < BLOCK / 32 ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, d);
+            if (lane >= d) t += y;
+        }
+        if (lane < BLOCK / 32) warp_tot[lane] = t;  // inclusive
+    }
+    __syncthreads();
+    const uint32_t before = wid > 0 ? warp_tot[wid - 1] : 0u;
+    out[threadIdx.x] = before + x - v;
+    const uint32_t total = warp_tot[BLOCK / 32 - 1];
+    return total;
+}
+
+// One diffusion window for BLOCK consecutive tets (device order).
+//  load   counts into shared memory; mobile entries of `cur` are zeroed as read
+//  A      each thread: its tet's propensities and first waiting time, in float;
+//         (double)dt > tau_k is tested as dt > tau_dn, tau_dn the largest float
+//         <= tau_k (the same decision); tets with an event are queued
+//  B      the queued tets' full SSA and trial counts, one queued tet per thread
+//  C      trial words of all the block's tets: Philox blocks of four words are
+//         spread evenly over the threads; each word moves or keeps one trial
+//         molecule; movers are added to the neighbour in `nxt` at once
+//  D      what stays is added to the tet's own entry of `nxt` (coalesced)
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2) step_kernel(const __grid_constant__ ModelDev m,
+                                                     const __grid_constant__ StepArgs a) {
+    extern __shared__ __align__(16) int32_t smem[];  // cnt [S][BLOCK], trial [S][BLOCK]
+    __shared__ __align__(16) uint4 s_thr[BLOCK];
+    __shared__ __align__(16) int4 s_nbr[BLOCK];
+    __shared__ __align__(16) uint32_t s_tet[BLOCK];
+    __shared__ __align__(16) float s_inv_nav[BLOCK];
+    __shared__ __align__(16) uint32_t s_mask[BLOCK];
+    __shared__ int32_t queue[BLOCK];
+    __shared__ uint32_t blk_start[BLOCK + 1];
+    __shared__ uint32_t words[BLOCK];
+    __shared__ uint32_t warp_tot[BLOCK / 32];
+    __shared__ int32_t nqueue;
+    __shared__ __align__(8) uint64_t bar;
+
+    const int S = m.S;
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * BLOCK;
+    const int64_t i = i0 + tid;
+    const int nlive = (int)min((int64_t)BLOCK, (int64_t)a.T - i0);
+    const bool live = tid < nlive;
+    int32_t *cnt_all = smem;
+    int32_t *trial_all = smem + (size_t)S * BLOCK;
+    const uint64_t window = a.window + (a.window_base ? *a.window_base : 0ull);
+    const uint32_t c0 = (uint32_t)window;
+    const uint32_t c3 = (uint32_t)(window >> 32) & 0x0FFFFFFFu;
+    const size_t Tpad = (size_t)a.Tpad;
+    uint32_t bad = 0;
+
+    // ---- load: the block's tile of every table, by TMA bulk copies into
+    // shared memory (rows padded to 16 bytes; the tables are padded to Tpad)
+    if (tid == 0) {
+        nqueue = 0;
+        mbar_init(&bar, 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t n4 = ((uint32_t)nlive + 3u) & ~3u;
+        const uint32_t bytes = (uint32_t)S * n4 * 4u + 2u * (uint32_t)nlive * 16u + n4 * 4u +
+                               (a.orig ? n4 * 4u : 0u) + (a.rmask ? n4 * 4u : 0u);
+        mbar_expect_tx(&bar, bytes);
+        for (int s = 0; s < S; ++s) bulk_g2s(cnt_all + s * BLOCK, a.cur + s * Tpad + i0, n4 * 4u, &bar);
+        bulk_g2s(s_thr, a.thr + i0, (uint32_t)nlive * 16u, &bar);
+        bulk_g2s(s_nbr, a.nbr + i0, (uint32_t)nlive * 16u, &bar);
+        bulk_g2s(s_inv_nav, a.inv_nav + i0, n4 * 4u, &bar);
+        if (a.orig) bulk_g2s(s_tet, a.orig + i0, n4 * 4u, &bar);
+        if (a.rmask) bulk_g2s(s_mask, a.rmask + i0, n4 * 4u, &bar);
+    }
+    if (!a.orig) s_tet[tid] = (uint32_t)i;
+    if (!a.rmask) s_mask[tid] = 0xFFFFFFFFu;
+    const bool arrived = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!arrived)) {
+        // the copies did not land in time: report, let them finish (bounded), skip the window
+        if (tid == 0) {
+            atomicOr(a.err, 4u);
+            mbar_wait_bounded(&bar, 0);
+        }
+        __syncthreads();
+        return;
+    }
+    if (live) {
+        for (int s = 0; s < S; ++s) {
+            const int32_t v = cnt_all[s * BLOCK + tid];
+            bad |= v < 0 ? 1u : 0u;
+            trial_all[s * BLOCK + tid] = v;
+            if ((m.diffusive >> s) & 1u) a.cur[s * Tpad + i] = 0;  // receives the window after next
+        }
+    }
+    __syncthreads();
+
+    // ---- A: does the tet's first reaction fall inside the window?
+    if (live && m.R > 0) {
+        const float inv_nav = s_inv_nav[tid];
+        const uint32_t active = s_mask[tid];
+        const int32_t *cnt = cnt_all + tid;
+        float a0 = 0.0f;
+#pragma unroll
+        for (int r = 0; r < kMaxReac; ++r) {
+            if (r < m.R) {
+                const float ar = ((active >> r) & 1u) ? propensity(m.reac[r], cnt, BLOCK, inv_nav) : 0.0f;
+                a0 = __fadd_rn(a0, ar);
+            }
+        }
+        if (a0 > 0.0f) {
+            const uint4 w = philox4x32_10(a.key0, a.key1, c0, s_tet[tid], 0u, (kPurposeReac << 28) | c3);
+            const float dt = __fdiv_rn(-steps_logf(unit24f(w.x)), a0);
+            if (!(dt > a.tau_dn)) queue[atomicAdd(&nqueue, 1)] = tid;
+        }
+    }
+    __syncthreads();
+
+    // ---- B: full SSA of the tets that react, packed onto the first threads
+    for (int q = tid; q < nqueue; q += BLOCK) {
+        const int t = queue[q];
+        bad |= ssa_tet<BLOCK>(m, a, cnt_all + t, trial_all + t, s_tet[t], c0, c3, s_inv_nav[t], s_mask[t]);
+    }
+    __syncthreads();
+
+    // ---- C: trial molecules of the whole block, four words per work item
+    uint32_t W = 0;
+    if (live) {
+        const uint4 A = s_thr[tid];
+        for (int s = 0; s < S; ++s) {
+            int32_t M = 0;
+            if ((m.diffusive >> s) & 1u) {
+                M = trial_all[s * BLOCK + tid];
+                if ((uint32_t)(((uint64_t)A.w * a.scale[s]) >> 31) == 0u) M = 0;
+            }
+            trial_all[s * BLOCK + tid] = M;
+            W += (uint32_t)M;
+        }
+    }
+    words[tid] = W;
+    const uint32_t total = block_exclusive_scan<BLOCK>((W + 3u) >> 2, blk_start, warp_tot);
+    if (tid == 0) blk_start[BLOCK] = total;
+    __syncthreads();
+    for (uint32_t item = tid; item < total; item += BLOCK) {
+        // the tet owning this item: last t with blk_start[t] <= item
+        int lo = 0, hi = nlive - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (blk_start[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const int t = lo;
+        const uint32_t b = item - blk_start[t];
+        const uint32_t Wt = words[t];
+        const uint32_t tet = s_tet[t];
+        const uint4 A = s_thr[t];
+        const int4 nb = s_nbr[t];
+        const int32_t *trial = trial_all + t;
+        // species of the first word of the item
+        uint32_t w = b << 2;
+        int s = 0;
+        uint32_t end = (uint32_t)trial[0];
+        while (w >= end) {
+            ++s;
+            end += (uint32_t)trial[s * BLOCK];
+        }
+        uint64_t R = a.scale[s];
+        uint32_t T0 = (uint32_t)(((uint64_t)A.x * R) >> 31), T1 = (uint32_t)(((uint64_t)A.y * R) >> 31);
+        uint32_t T2 = (uint32_t)(((uint64_t)A.z * R) >> 31), T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
+        const uint4 rw = philox4x32_10(a.key0, a.key1, c0, tet, b, (kPurposeDiff << 28) | c3);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (w < Wt) {
+                if (w >= end) {  // next species with trial molecules
+                    do {
+                        ++s;
+                        end += (uint32_t)trial[s * BLOCK];
+                    } while (w >= end);
+                    R = a.scale[s];
+                    T0 = (uint32_t)(((uint64_t)A.x * R) >> 31);
+                    T1 = (uint32_t)(((uint64_t)A.y * R) >> 31);
+                    T2 = (uint32_t)(((uint64_t)A.z * R) >> 31);
+                    T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
+                }
+                // face f when T_{f-1} <= x < T_f (cumulative thresholds), stay when x >= T3
+                const uint32_t x = word_of(rw, k) >> 1;
+                if (x < T3) {
+                    const int nbr = x < T0 ? nb.x : x < T1 ? nb.y : x < T2 ? nb.z : nb.w;
+                    atomicAdd(a.nxt + s * Tpad + nbr, 1);
+                    atomicSub(&cnt_all[s * BLOCK + t], 1);
+                }
+                ++w;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- D: the molecules that stay (immobile species: written by this tet alone)
+    if (live) {
+        for (int s = 0; s < S; ++s) {
+            const int32_t N = cnt_all[s * BLOCK + tid];
+            int32_t *out = a.nxt + s * Tpad + i;
+            if ((m.diffusive >> s) & 1u) {
+                if (N) atomicAdd(out, N);
+            } else {
+                *out = N;
+            }
+        }
+    }
+    if (bad) atomicOr(a.err, bad);
+}
+
+__global__ void philox_test_kernel(uint32_t k0, uint32_t k1, const uint4 *ctr, int64_t n, uint4 *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = ctr[i];
+    out[i] = philox4x32_10(k0, k1, c.x, c.y, c.z, c.w);
+}
+
+__global__ void logf_test_kernel(const float *x, int64_t n, float *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = steps_logf(x[i]);
+}
+
+__global__ void add_u64_kernel(uint64_t *p, uint64_t v) { *p += v; }
+
+template <int BLOCK>
+int launch_step_t(const ModelDev &m, const StepArgs &a, void *stream) {
+    const int64_t grid = (a.T + BLOCK - 1) / BLOCK;
+    const size_t smem = 2 * (size_t)m.S * BLOCK * sizeof(int32_t);
+    static size_t static_smem = [] {
+        cudaFuncAttributes fa{};
+        return cudaFuncGetAttributes(&fa, step_kernel<BLOCK>) == cudaSuccess ? fa.sharedSizeBytes : (size_t)0;
+    }();
+    if (smem + static_smem > 48 * 1024) {  // opt in to more than the default 48 KB per block
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) {
+            set_error(std::string("step kernel shared memory: ") + cudaGetErrorString(e));
+            return STEPS_ERR_CUDA;
+        }
+    }
+    step_kernel<BLOCK><<<(unsigned)grid, BLOCK, smem, (cudaStream_t)stream>>>(m, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("step kernel launch: ") + cudaGetErrorString(e));
+        return STEPS_ERR_CUDA;
+    }
+    return STEPS_OK;
+}
+
+}  // namespace
+
+int launch_step(const ModelDev &m, const StepArgs &a, int block, void *stream) {
+    if (a.T <= 0) return STEPS_OK;
+    switch (block) {
+    case 64: return launch_step_t<64>(m, a, stream);
+    case 128: return launch_step_t<128>(m, a, stream);
+    case 512: return launch_step_t<512>(m, a, stream);
+    default: return launch_step_t<256>(m, a, stream);
+    }
+}
+
+int launch_philox_test(uint64_t seed, const uint32_t *d_ctr, int64_t n, uint32_t *d_out, void *stream) {
+    if (n <= 0) return STEPS_OK;
+    philox_test_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        (uint32_t)seed, (uint32_t)(seed >> 32), (const uint4 *)d_ctr, n, (uint4 *)d_out);
+    return cudaGetLastError() == cudaSuccess ? STEPS_OK : STEPS_ERR_CUDA;
+}
+
+int launch_logf_test(const float *d_x, int64_t n, float *d_out, void *stream) {
+    if (n <= 0) return STEPS_OK;
+    logf_test_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(d_x, n, d_out);
+    return cudaGetLastError() == cudaSuccess ? STEPS_OK : STEPS_ERR_CUDA;
+}
+
+int launch_add_u64(uint64_t *p, uint64_t v, void *stream) {
+    add_u64_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(p, v);
+    return cudaGetLastError() == cudaSuccess ? STEPS_OK : STEPS_ERR_CUDA;
+}
+
+}  // namespace steps

@@ -1,0 +1,89 @@
+"""CPU checks of the C ABI: the CUDA library builds for sm_103a, loads, exports
+every function include/*.h declares, and its host-only calls (mesh and model
+construction, which launch nothing) validate their inputs. No compute call
+is made here: that needs a GPU."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1610_02258_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1610_02258_gb300.build import build
+    build()
+    from paper_1610_02258_gb300 import capi as c
+    return c
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \t\*]*?\b(steps_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(capi):
+    declared = _declared()
+    assert len(declared) >= 20
+    for name in sorted(declared):
+        assert hasattr(capi.lib, name), name
+    assert declared == set(capi.EXPORTS)
+
+
+def test_options_defaults(capi):
+    o = capi.steps_options_default()
+    assert (o.occupancy, o.reorder, o.block, o.use_graph) == (1, 1, 256, 1)
+
+
+def test_mesh_validation_matches_oracle_rules(capi):
+    verts, tets = I.kuhn_box_mesh(2, 1, 1, 1.0)
+    h = capi.steps_mesh_create(verts, tets)
+    assert capi.steps_mesh_num_tets(h) == 12
+    capi.steps_mesh_destroy(h)
+    with pytest.raises(capi.StepsError) as e:
+        capi.steps_mesh_create(verts, np.concatenate([tets, tets[:1]]))
+    assert e.value.code == -2 and "more than two" in str(e.value)
+    bad = tets.copy()
+    bad[3] = [0, 1, 2, 2]
+    with pytest.raises(capi.StepsError) as e:
+        capi.steps_mesh_create(verts, bad)
+    assert e.value.code == -2
+    bad = tets.copy()
+    bad[0, 1] = len(verts)
+    with pytest.raises(capi.StepsError) as e:
+        capi.steps_mesh_create(verts, bad)
+    assert e.value.code == -2
+    with pytest.raises(capi.StepsError) as e:
+        capi.steps_mesh_create(verts, tets[:0])
+    assert e.value.code == -1
+
+
+def test_model_validation(capi):
+    m = I.config1_model()
+    h = capi.steps_model_create(m.diff, m.lhs, m.rhs, m.k)
+    capi.steps_model_destroy(h)
+    # zero reactions is a valid (pure diffusion) model
+    h = capi.steps_model_create([1e-12], np.zeros((0, 1)), np.zeros((0, 1)), np.zeros(0))
+    capi.steps_model_destroy(h)
+    with pytest.raises(capi.StepsError) as e:  # third order
+        capi.steps_model_create([1e-12, 0.0], [[2, 1]], [[0, 0]], [1.0])
+    assert e.value.code == -3
+    with pytest.raises(capi.StepsError) as e:  # negative rate
+        capi.steps_model_create([1e-12], [[1]], [[0]], [-1.0])
+    assert e.value.code == -3
+    with pytest.raises(capi.StepsError) as e:  # negative D
+        capi.steps_model_create([-1e-12], [[1]], [[0]], [1.0])
+    assert e.value.code == -3
+    with pytest.raises(capi.StepsError) as e:  # too many species
+        capi.steps_model_create(np.zeros(33), np.zeros((0, 33)), np.zeros((0, 33)), np.zeros(0))
+    assert e.value.code == -1

@@ -1,0 +1,240 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Bar: integer counts are compared element by element. Everything the
+diffusion operator does is integer work and must be bit-exact. The reaction
+operator takes its decisions in float like the oracle's kernel-precision mode
+(prec=32), which evaluates the same IEEE operations in the same order, so whole
+runs are bit-exact against it; against the FP64 oracle the reaction phase is
+compared in distribution (two-sample KS p > 0.01, means within 3 standard
+errors over 10^4 replicates)."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from oracle import END, OCC
+from paper_1610_02258_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_02258_gb300.build import build
+    build()
+    from paper_1610_02258_gb300 import capi as c
+    return c
+
+
+def run_both(capi, verts, tets, model, counts, seed, t_end, occ=OCC, masks=None, prec=32, **kw):
+    g = capi.Simulation(verts, tets, model, seed, occupancy=occ, **kw)
+    g.set_counts(counts)
+    o = oracle.OracleSim(verts, tets, model, seed=seed, occ=occ, prec=prec)
+    o.set_counts(counts)
+    for r, m in (masks or {}).items():
+        g.set_reac_mask(r, m)
+        o.set_reac_mask(r, m)
+    assert g.tau == o.tau
+    for t in np.atleast_1d(t_end):
+        g.run(t)
+        o.run(t)
+    assert g.windows == o.windows
+    assert g.time == o.time
+    return g.get_counts(), o.get_counts(), g, o
+
+
+# ------------------------------------------------------------------ building blocks
+
+def test_philox_bit_exact(capi):
+    rng = np.random.default_rng(3)
+    ctr = rng.integers(0, 2**32, size=(1 << 16, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    for seed in [0, 3, (1 << 64) - 1, 0x0123456789ABCDEF]:
+        assert np.array_equal(capi.steps_debug_philox(seed, ctr), oracle.philox_array(seed, ctr))
+
+
+def test_logf_bit_exact_on_every_uniform(capi):
+    """The kernel's float log agrees bit for bit with the oracle's on all 2^24
+    uniforms (m+1)/2^24 the reaction operator can draw, and on random floats."""
+    u = ((np.arange(1 << 24, dtype=np.float64) + 1) / 2**24).astype(np.float32)
+    assert np.array_equal(capi.steps_debug_logf(u).view(np.uint32), oracle.logf32_array(u).view(np.uint32))
+    x = np.exp(np.random.default_rng(4).uniform(-80, 80, 1 << 16)).astype(np.float32)
+    assert np.array_equal(capi.steps_debug_logf(x).view(np.uint32), oracle.logf32_array(x).view(np.uint32))
+
+
+# ------------------------------------------------------------------ whole runs, bit-exact
+
+@pytest.mark.parametrize("reorder", [0, 1])
+def test_pure_diffusion_bit_exact(capi, reorder):
+    """Diffusion only (no reactions): integer work end to end, including the
+    shortened last window."""
+    w = I.config1()
+    m = I.model_from_lists(["A", "B"], [1e-11, 2.5e-12], [])
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, m, w.counts[:2], 17, w.t_end, reorder=reorder)
+    assert g.windows == 14
+    assert np.array_equal(gc, oc)
+    assert np.array_equal(gc.sum(axis=1), w.counts[:2].sum(axis=1))
+
+
+@pytest.mark.parametrize("occ", [OCC, END])
+def test_config1_reaction_diffusion_bit_exact(capi, occ):
+    w = I.config1()
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, w.model, w.counts, w.seed, w.t_end, occ=occ)
+    assert o.events > 0
+    assert np.array_equal(gc, oc)
+
+
+@pytest.mark.parametrize("occ", [OCC, END])
+def test_irregular_mesh_bit_exact_many_tiles_ragged_tail(capi, occ):
+    """Jittered box of 12x17x17 cubes = 20,808 tets (81 blocks of 256 and a
+    ragged tail of 72), 10-species / 20-reaction network, 5 ms (24 full
+    windows and a shortened one)."""
+    w = I.config2(nx=12, t_end=5e-3)
+    assert w.n_tets % 256 != 0
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, w.model, w.counts, w.seed, w.t_end, occ=occ)
+    assert o.events > 1000
+    assert np.array_equal(gc, oc)
+
+
+def test_full_size_config2_whole_run_bit_exact(capi):
+    """The benchmark workload at full size (294,780 tets, 20 ms, 99 windows),
+    default launch configuration (Morton order, CUDA graph, 256 threads)."""
+    w = I.config2()
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, w.model, w.counts, w.seed, w.t_end)
+    assert g.windows == 99
+    assert np.array_equal(gc, oc)
+
+
+def test_region_mask_and_zero_order_influx_bit_exact(capi):
+    """Reaction masks (influx only in the first 5% of tets) on a small
+    dendrite-shaped mesh with the 20-species calcium network."""
+    w = I.config3(h=0.5e-6, t_end=0.2e-3)
+    assert 20000 < w.n_tets < 80000
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, w.model, w.counts, w.seed, w.t_end, masks=w.reac_masks)
+    assert o.events > 0
+    assert np.array_equal(gc, oc)
+
+
+def test_resume_on_window_grid_equals_single_run(capi):
+    w = I.config2(nx=4, t_end=3e-3)
+    a = capi.from_workload(w)
+    tau = a.tau
+    a.run(7 * tau)
+    a.run(w.t_end)
+    b = capi.from_workload(w)
+    b.run(w.t_end)
+    assert np.array_equal(a.get_counts(), b.get_counts())
+    assert a.windows == b.windows
+
+
+def test_launch_shape_order_and_graph_do_not_change_results(capi):
+    w = I.config2(nx=6, t_end=4e-3)
+    ref = None
+    for kw in [dict(), dict(use_graph=False), dict(block=64), dict(block=128), dict(block=512),
+               dict(reorder=0), dict(reorder=0, use_graph=False, block=512)]:
+        s = capi.from_workload(w, **kw)
+        s.run(w.t_end)
+        c = s.get_counts()
+        if ref is None:
+            ref = c
+        assert np.array_equal(c, ref), kw
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_edge_single_tet_and_empty_counts(capi):
+    verts, tets = I.isolated_tets(1)
+    m = I.config1_model()
+    c = np.array([[3], [4], [0]], np.int32)
+    gc, oc, *_ = run_both(capi, verts, tets, m, c, 5, 1e-2)
+    assert np.array_equal(gc, oc)
+    w = I.config1()
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, w.model, np.zeros_like(w.counts), 5, 2e-3)
+    assert gc.sum() == 0 and np.array_equal(gc, oc)
+
+
+def test_edge_immobile_species_and_no_diffusion(capi):
+    w = I.config1()
+    m = I.model_from_lists(["A", "B", "C"], [0.0, 1e-11, 0.0],
+                           [(["A", "B"], ["C"], 1e8), (["C"], ["A", "B"], 10.0)])
+    gc, oc, *_ = run_both(capi, w.verts, w.tets, m, w.counts, 6, 3e-3)
+    assert np.array_equal(gc, oc)
+    m = I.model_from_lists(["A", "B", "C"], [0.0, 0.0, 0.0],
+                           [(["A", "B"], ["C"], 1e8), (["C"], ["A", "B"], 10.0)])
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, m, w.counts, 6, [1e-3, 3e-3])
+    assert math.isinf(g.tau) and g.windows == 2
+    assert np.array_equal(gc, oc)
+
+
+def test_edge_large_counts_and_p_equal_one(capi):
+    """10^5 molecules in one tet (a long per-molecule loop) and tets whose
+    leave probability is exactly 1 (the fastest tets of a regular grid)."""
+    w = I.config1()
+    m = I.model_from_lists(["A"], [1e-11], [])
+    c = np.zeros((1, w.n_tets), np.int32)
+    c[0, 777] = 100000
+    gc, oc, *_ = run_both(capi, w.verts, w.tets, m, c, 8, [0.0, 3e-3])
+    assert np.array_equal(gc, oc) and gc.sum() == 100000
+
+
+def test_edge_noop_and_bad_arguments(capi):
+    w = I.config1()
+    s = capi.from_workload(w)
+    s.run(0.0)
+    assert s.windows == 0
+    s.run(-1.0)
+    assert s.windows == 0
+    bad = w.counts.copy()
+    bad[0, 0] = -1
+    with pytest.raises(capi.StepsError) as e:
+        s.set_counts(bad)
+    assert e.value.code == -1
+    with pytest.raises(capi.StepsError):
+        s.run(float("nan"))
+
+
+# ------------------------------------------------------------------ statistics vs the FP64 oracle
+
+def test_reaction_phase_matches_fp64_oracle_in_distribution(capi):
+    """10^4 well-mixed replicates (isolated tets) of A + B <-> C: the float
+    kernel against the FP64 oracle with a different seed, two-sample KS
+    p > 0.01 and means within 3 standard errors; both against the exact CME."""
+    n, N0, kf, kb, t = 10000, 30, 1e8, 50.0, 4e-3
+    verts, tets = I.isolated_tets(n)
+    m = I.model_from_lists(["A", "B", "C"], [0.0, 0.0, 0.0],
+                           [(["A", "B"], ["C"], kf), (["C"], ["A", "B"], kb)])
+    c = np.zeros((3, n), np.int32)
+    c[0] = N0
+    c[1] = N0 + 5
+    g = capi.Simulation(verts, tets, m, 101)
+    g.set_counts(c)
+    g.run(t)
+    gx = g.get_counts()[2]
+    o = oracle.OracleSim(verts, tets, m, seed=202, prec=64)
+    o.set_counts(c)
+    o.run(t)
+    ox = o.get_counts()[2]
+    assert stats.ks_2samp(gx, ox).pvalue > 0.01
+    se = math.sqrt(gx.var() / n + ox.var() / n)
+    assert abs(gx.mean() - ox.mean()) < 3 * se
+
+
+def test_conservation_full_config2(capi):
+    w = I.config2()
+    s = capi.from_workload(w)
+    s.run(w.t_end)
+    c = s.get_counts()
+    assert c.min() >= 0
+    # each reaction of the random network conserves nothing in general, but
+    # without reactions every species total is conserved
+    m = I.model_from_lists(w.model.names, w.model.diff, [])
+    s2 = capi.Simulation(w.verts, w.tets, m, 1)
+    s2.set_counts(w.counts)
+    s2.run(w.t_end)
+    assert np.array_equal(s2.get_counts().sum(axis=1), w.counts.sum(axis=1))
