@@ -135,6 +135,34 @@ __device__ __forceinline__ float propensity(const ReacDesc &d, const int32_t *cn
     }
 }
 
+// Stochastic rounding of a mean occupancy: floor(nbar) + [u < nbar - floor(nbar)]
+// with u = (w + 1/2) 2^-32. Both the floor and the comparison are exact real
+// operations on the double nbar >= 0, evaluated here on its bit pattern with
+// integer arithmetic (value = mant 2^-sh): the same result as the double
+// operations, without using the FP64 pipe.
+__device__ __forceinline__ long long round_trials(double nbar, uint32_t w) {
+    const uint64_t bits = (uint64_t)__double_as_longlong(nbar);
+    const int e = (int)((bits >> 52) & 0x7ffu);
+    if (e == 0 || (bits >> 63)) return 0;  // zero (or negative, not reached): no trials
+    const uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = 1075 - e;  // fraction bits of mant
+    if (sh <= 0) return (long long)(mant << min(-sh, 10));  // integral (counts are < 2^31)
+    long long fl;
+    uint64_t f;
+    if (sh >= 64) {
+        fl = 0;
+        f = mant;
+    } else {
+        fl = (long long)(mant >> sh);
+        f = mant & ((1ull << sh) - 1);
+    }
+    // u < f 2^-sh  <=>  (2w + 1) 2^sh < f 2^33; beyond sh = 90 the fraction is < 2^-38 < u
+    if (sh > 90) return fl;
+    const unsigned __int128 lhs = (unsigned __int128)(2ull * w + 1ull) << sh;
+    const unsigned __int128 rhs = (unsigned __int128)f << 33;
+    return fl + (lhs < rhs ? 1 : 0);
+}
+
 // Reaction SSA operator for one tet over tau_k (Algorithm 1, reaction part):
 // Gillespie's direct method with float propensities and double time, and
 // the time-weighted occupancy of every species a fired reaction changes.
@@ -165,10 +193,18 @@ __device__ uint32_t ssa_tet(const ModelDev &m, const StepArgs &a, int32_t *cnt, 
             bad |= 2u;
             break;
         }
-        const uint4 w = philox4x32_10(a.key0, a.key1, c0, tet, j++, (kPurposeReac << 28) | c3);
+        const uint4 w = philox4x32_10(a.key0, a.key1, c0, tet, j, (kPurposeReac << 28) | c3);
         const float dt = __fdiv_rn(-steps_logf(unit24f(w.x)), a0);
-        const double dt_new = __dadd_rn(dt_acc, (double)dt);
-        if (dt_new > a.tau_k) break;
+        double dt_new;
+        if (j == 0) {
+            // 0 + (double)dt is exact, and (double)dt > tau_k <=> dt > tau_dn
+            if (dt > a.tau_dn) break;
+            dt_new = (double)dt;
+        } else {
+            dt_new = __dadd_rn(dt_acc, (double)dt);
+            if (dt_new > a.tau_k) break;
+        }
+        ++j;
         const float target = __fmul_rn(unit24f(w.y), a0);
         float c = 0.0f;
         int pick = -1;
@@ -190,10 +226,11 @@ __device__ uint32_t ssa_tet(const ModelDev &m, const StepArgs &a, int32_t *cnt, 
         for (int q = 0; q < d.nchg; ++q) {
             const int s = d.chg_s[q];
             const int32_t n = cnt[s * BLOCK];
-            const bool seen = (touched >> s) & 1u;
-            const double o = seen ? O[s] : 0.0;
-            const double ts = seen ? tS[s] : 0.0;
-            O[s] = __dadd_rn(o, __dmul_rn((double)n, __dsub_rn(dt_acc, ts)));
+            if ((touched >> s) & 1u) {
+                O[s] = __dadd_rn(O[s], __dmul_rn((double)n, __dsub_rn(dt_acc, tS[s])));
+            } else {
+                O[s] = __dmul_rn((double)n, dt_acc);  // 0 + n (dt - 0): both steps exact
+            }
             tS[s] = dt_acc;
             touched |= 1u << s;
             cnt[s * BLOCK] = n + d.chg_d[q];
@@ -212,21 +249,20 @@ __device__ uint32_t ssa_tet(const ModelDev &m, const StepArgs &a, int32_t *cnt, 
             // Nbar = (O_S + N_S (tau - t_S)) / tau, stochastically rounded, clamped to N_S
             const double occ = __dadd_rn(O[s], __dmul_rn((double)N, __dsub_rn(a.tau_k, tS[s])));
             const double nbar = __dmul_rn(occ, a.inv_tau_k);
-            const double fl = floor(nbar);
-            const double frac = __dsub_rn(nbar, fl);
             if ((uint32_t)(s >> 2) != rblk) {
                 rblk = (uint32_t)(s >> 2);
                 rb = philox4x32_10(a.key0, a.key1, c0, tet, rblk, (kPurposeRound << 28) | c3);
             }
-            const double u = __dmul_rn(__dadd_rn((double)word_of(rb, s & 3), 0.5), 2.3283064365386963e-10);
-            long long mm = (long long)fl + (u < frac ? 1 : 0);
-            mm = mm < 0 ? 0 : mm;
+            const long long mm = round_trials(nbar, word_of(rb, s & 3));
             M = mm > N ? N : (int32_t)mm;
         }
         trial[s * BLOCK] = M;
     }
     return bad;
 }
+
+// Trial words per phase-C work item (two Philox blocks).
+constexpr uint32_t kItemWords = 8;
 
 // Block-wide exclusive scan of one value per thread; returns the total.
 template <int BLOCK>
@@ -380,7 +416,7 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2) step_kernel(const __g
         }
     }
     words[tid] = W;
-    const uint32_t total = block_exclusive_scan<BLOCK>((W + 3u) >> 2, blk_start, warp_tot);
+    const uint32_t total = block_exclusive_scan<BLOCK>((W + kItemWords - 1u) / kItemWords, blk_start, warp_tot);
     if (tid == 0) blk_start[BLOCK] = total;
     __syncthreads();
     for (uint32_t item = tid; item < total; item += BLOCK) {
@@ -392,14 +428,13 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2) step_kernel(const __g
             else hi = mid - 1;
         }
         const int t = lo;
-        const uint32_t b = item - blk_start[t];
         const uint32_t Wt = words[t];
         const uint32_t tet = s_tet[t];
         const uint4 A = s_thr[t];
         const int4 nb = s_nbr[t];
         const int32_t *trial = trial_all + t;
-        // species of the first word of the item
-        uint32_t w = b << 2;
+        // species of the item's first word
+        uint32_t w = (item - blk_start[t]) * kItemWords;
         int s = 0;
         uint32_t end = (uint32_t)trial[0];
         while (w >= end) {
@@ -409,29 +444,32 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2) step_kernel(const __g
         uint64_t R = a.scale[s];
         uint32_t T0 = (uint32_t)(((uint64_t)A.x * R) >> 31), T1 = (uint32_t)(((uint64_t)A.y * R) >> 31);
         uint32_t T2 = (uint32_t)(((uint64_t)A.z * R) >> 31), T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
-        const uint4 rw = philox4x32_10(a.key0, a.key1, c0, tet, b, (kPurposeDiff << 28) | c3);
+#pragma unroll 1
+        for (int half = 0; half < kItemWords / 4 && w < Wt; ++half) {
+            const uint4 rw = philox4x32_10(a.key0, a.key1, c0, tet, w >> 2, (kPurposeDiff << 28) | c3);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (w < Wt) {
-                if (w >= end) {  // next species with trial molecules
-                    do {
-                        ++s;
-                        end += (uint32_t)trial[s * BLOCK];
-                    } while (w >= end);
-                    R = a.scale[s];
-                    T0 = (uint32_t)(((uint64_t)A.x * R) >> 31);
-                    T1 = (uint32_t)(((uint64_t)A.y * R) >> 31);
-                    T2 = (uint32_t)(((uint64_t)A.z * R) >> 31);
-                    T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
+            for (int k = 0; k < 4; ++k) {
+                if (w < Wt) {
+                    if (w >= end) {  // next species with trial molecules
+                        do {
+                            ++s;
+                            end += (uint32_t)trial[s * BLOCK];
+                        } while (w >= end);
+                        R = a.scale[s];
+                        T0 = (uint32_t)(((uint64_t)A.x * R) >> 31);
+                        T1 = (uint32_t)(((uint64_t)A.y * R) >> 31);
+                        T2 = (uint32_t)(((uint64_t)A.z * R) >> 31);
+                        T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
+                    }
+                    // face f when T_{f-1} <= x < T_f (cumulative thresholds), stay when x >= T3
+                    const uint32_t x = word_of(rw, k) >> 1;
+                    if (x < T3) {
+                        const int nbr = x < T0 ? nb.x : x < T1 ? nb.y : x < T2 ? nb.z : nb.w;
+                        atomicAdd(a.nxt + s * Tpad + nbr, 1);
+                        atomicSub(&cnt_all[s * BLOCK + t], 1);
+                    }
+                    ++w;
                 }
-                // face f when T_{f-1} <= x < T_f (cumulative thresholds), stay when x >= T3
-                const uint32_t x = word_of(rw, k) >> 1;
-                if (x < T3) {
-                    const int nbr = x < T0 ? nb.x : x < T1 ? nb.y : x < T2 ? nb.z : nb.w;
-                    atomicAdd(a.nxt + s * Tpad + nbr, 1);
-                    atomicSub(&cnt_all[s * BLOCK + t], 1);
-                }
-                ++w;
             }
         }
     }
