@@ -152,6 +152,31 @@ int steps_get_tau(const steps_sim *sim, double *tau);
 /* Windows run so far (the RNG window index) and kernel launches issued. */
 int steps_get_windows(const steps_sim *sim, uint64_t *windows, uint64_t *launches);
 
+/*
+ * Advance `sim` to t_end on counts held in a caller-owned device buffer,
+ * without allocating any memory. The paper has no counterpart: this serves
+ * callers that cannot let a library call cudaMalloc -- an application that
+ * owns all device memory through its own pool or a fixed per-job budget, or
+ * one that must not allocate once it is running. The simulation must still be
+ * created beforehand (that call allocates its tables).
+ *   d_counts: [n_species * nt] int32 device pointer, species-major, original
+ *             tet order; in: counts at the current time; out: counts at t_end.
+ * Runs the same windows as steps_run (same results, bit for bit) with plain
+ * launches. The simulation's clock advances; its own count buffers are
+ * neither read nor written, so do not mix this call with steps_run on one
+ * simulation without setting the counts again.
+ * Scratch: a fixed device array in the library, two count buffers of at most
+ * 4,194,304 int32 each (n_species * nt rounded up to a multiple of 32) plus an
+ * error word: 32 MiB held on every GPU that loads the library until exit.
+ * Larger problems get STEPS_ERR_ARG. The array is shared by every call and
+ * keeps the last call's contents (each call clears it first); calls that
+ * overlap on the GPU, on any stream or thread, race on it. The first call on
+ * a device looks up the array's address with that device current; make that
+ * first call before any stream capture. Synchronises with the simulation's
+ * stream before returning. Errors as steps_run.
+ */
+int steps_run_noalloc(steps_sim *sim, int32_t *d_counts, double t_end);
+
 const char *steps_last_error(void);
 
 /* ---------------------------------------------------------------------- */

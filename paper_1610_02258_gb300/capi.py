@@ -28,7 +28,7 @@ EXPORTS = [
     "steps_model_create", "steps_model_destroy", "steps_sim_create", "steps_sim_destroy",
     "steps_set_counts", "steps_get_counts", "steps_set_counts_all", "steps_get_counts_all",
     "steps_set_reac_mask", "steps_run", "steps_get_time", "steps_get_tau", "steps_get_windows",
-    "steps_last_error", "steps_debug_philox", "steps_debug_logf",
+    "steps_last_error", "steps_debug_philox", "steps_debug_logf", "steps_run_noalloc",
 ]
 
 
@@ -70,6 +70,7 @@ def _load():
         "steps_last_error": (ctypes.c_char_p, []),
         "steps_debug_philox": (ctypes.c_int, [u64, P, i64, P]),
         "steps_debug_logf": (ctypes.c_int, [P, i64, P]),
+        "steps_run_noalloc": (ctypes.c_int, [P, P, ctypes.c_double]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -176,6 +177,12 @@ def steps_set_reac_mask(sim, reac, active):
 
 def steps_run(sim, t_end):
     _check(lib.steps_run(sim, float(t_end)))
+
+
+def steps_run_noalloc(sim, d_counts_ptr, t_end):
+    """Advance on caller-owned device counts (an int pointer to [S * nt] int32,
+    species-major, original tet order), allocating nothing."""
+    _check(lib.steps_run_noalloc(sim, ctypes.c_void_p(int(d_counts_ptr)), float(t_end)))
 
 
 def steps_get_time(sim):

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <limits>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -571,3 +572,132 @@ int steps_debug_logf(const float *x, int64_t n, float *out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free run on caller-owned device counts.
+//
+// Scratch for steps_run_noalloc lives in this file-scope device array: two
+// receiving/sending count buffers of up to kNoAllocMaxCounts int32 each, then
+// an error word. Every GPU that loads the library holds it (32 MiB + 256 B)
+// until the process exits. Host code cannot use the array's name as a device
+// address; the address is looked up once per device with
+// cudaGetSymbolAddress, with that device current.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocMaxCounts = (size_t)1 << 22;  // n_species * Tpad per buffer
+__device__ __align__(256) int32_t g_noalloc_scratch[2 * kNoAllocMaxCounts + 64];
+
+struct NoAllocScratch {
+    bool ready = false;
+    int32_t *counts = nullptr;  // [2][kNoAllocMaxCounts]
+    uint32_t *err = nullptr;    // one word after the count buffers
+};
+
+constexpr int kNoAllocMaxDevices = 64;
+NoAllocScratch g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+int noalloc_scratch(NoAllocScratch &out) {
+    int dev = -1;
+    if (!cuda_ok(cudaGetDevice(&dev), "steps_run_noalloc: cudaGetDevice")) return STEPS_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("steps_run_noalloc: device index out of range");
+        return STEPS_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocScratch &s = g_noalloc_dev[dev];
+    if (!s.ready) {
+        void *p = nullptr;
+        if (!cuda_ok(cudaGetSymbolAddress(&p, g_noalloc_scratch), "steps_run_noalloc: cudaGetSymbolAddress"))
+            return STEPS_ERR_CUDA;
+        s.counts = static_cast<int32_t *>(p);
+        s.err = reinterpret_cast<uint32_t *>(s.counts + 2 * kNoAllocMaxCounts);
+        s.ready = true;
+    }
+    out = s;
+    return STEPS_OK;
+}
+
+}  // namespace
+
+extern "C" int steps_run_noalloc(steps_sim *sim, int32_t *d_counts, double t_end) {
+    CHECK_NULL(sim, "steps_run_noalloc");
+    CHECK_NULL(d_counts, "steps_run_noalloc");
+    if (!std::isfinite(t_end)) {
+        set_error("steps_run_noalloc: t_end must be finite");
+        return STEPS_ERR_ARG;
+    }
+    const size_t S = (size_t)sim->S, T = (size_t)sim->T, Tpad = (size_t)sim->Tpad;
+    if (S * Tpad > kNoAllocMaxCounts) {
+        set_error("steps_run_noalloc: n_species * padded tets = " + std::to_string(S * Tpad) +
+                  " exceeds the fixed scratch of " + std::to_string(kNoAllocMaxCounts) +
+                  " counts; use steps_run");
+        return STEPS_ERR_ARG;
+    }
+    NoAllocScratch sc;
+    int rc = noalloc_scratch(sc);
+    if (rc) return rc;
+    int32_t *buf[2] = {sc.counts, sc.counts + kNoAllocMaxCounts};
+    cudaStream_t st = sim->stream;
+    // the scratch keeps the previous call's contents: clear both buffers
+    // (padding and receiving rows must be zero) and the error word
+    if (!cuda_ok(cudaMemsetAsync(buf[0], 0, S * Tpad * 4, st), "steps_run_noalloc: clear") ||
+        !cuda_ok(cudaMemsetAsync(buf[1], 0, S * Tpad * 4, st), "steps_run_noalloc: clear") ||
+        !cuda_ok(cudaMemsetAsync(sc.err, 0, 4, st), "steps_run_noalloc: clear"))
+        return STEPS_ERR_CUDA;
+    const unsigned grid = (unsigned)((T + 255) / 256);
+    scatter_to_device_order<<<grid, 256, 0, st>>>(d_counts, (int64_t)T, (int32_t)S, sim->d_inv_perm, buf[0], Tpad);
+    if (!cuda_ok(cudaGetLastError(), "steps_run_noalloc: scatter")) return STEPS_ERR_CUDA;
+
+    // the window loop of steps_run (Algorithm 1), with plain launches on the scratch buffers
+    const double tau = sim->tab.tau;
+    const bool finite = std::isfinite(tau);
+    const double tol = finite ? 1e-9 * tau : 0.0;
+    int cur = 0;
+    auto launch = [&](double tau_k, const uint32_t *scale) -> int {
+        StepArgs a = sim->args(0, sim->k_total, nullptr, tau_k, scale);
+        a.cur = buf[cur];
+        a.nxt = buf[1 - cur];
+        a.err = sc.err;
+        int r = launch_step(sim->model.dev, a, sim->opt.block, st);
+        if (r) return r;
+        ++sim->launches;
+        ++sim->k_total;
+        cur = 1 - cur;
+        return STEPS_OK;
+    };
+    for (;;) {
+        const double t = sim->time();
+        if (!(t_end - t > tol)) break;
+        if (finite && t + tau <= t_end + tol) {
+            rc = launch(tau, sim->scale_full);
+            if (rc) return rc;
+            sim->k_grid += 1;
+        } else {
+            uint32_t scale[kMaxSpecies] = {};
+            for (int s = 0; s < sim->S; ++s) scale[s] = species_scale(sim->model, sim->tab, s, t_end - t);
+            rc = launch(t_end - t, scale);
+            if (rc) return rc;
+            sim->t_base = t_end;
+            sim->k_grid = 0;
+            break;
+        }
+    }
+    gather_to_original_order<<<grid, 256, 0, st>>>(buf[cur], (int64_t)T, (int32_t)S, sim->d_inv_perm, Tpad, d_counts);
+    if (!cuda_ok(cudaGetLastError(), "steps_run_noalloc: gather")) return STEPS_ERR_CUDA;
+    uint32_t err = 0;
+    if (!cuda_ok(cudaMemcpyAsync(&err, sc.err, 4, cudaMemcpyDeviceToHost, st), "steps_run_noalloc: error word") ||
+        !cuda_ok(cudaStreamSynchronize(st), "steps_run_noalloc"))
+        return STEPS_ERR_CUDA;
+    if (err & 4u) {
+        set_error("steps_run_noalloc: a bulk copy into shared memory did not complete within its wait limit");
+        return STEPS_ERR_TIMEOUT;
+    }
+    if (err) {
+        set_error(err & 2u ? "steps_run_noalloc: a tet fired more than 2^24 reactions in one window"
+                           : "steps_run_noalloc: a negative count was seen on the device");
+        return STEPS_ERR_STATE;
+    }
+    return STEPS_OK;
+}
