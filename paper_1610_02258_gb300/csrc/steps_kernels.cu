@@ -170,7 +170,7 @@ __device__ __forceinline__ long long round_trials(double nbar, uint32_t w) {
 // holds the integer trial count of every diffusive species the reactions
 // changed (mean occupancy, stochastically rounded, clamped to the end count;
 // or the end count in END mode). Returns error bits.
-template <int BLOCK>
+template <int BLOCK, int RM>
 __device__ uint32_t ssa_tet(const ModelDev &m, const StepArgs &a, int32_t *cnt, int32_t *trial, uint32_t tet,
                             uint32_t c0, uint32_t c3, float inv_nav, uint32_t active) {
     uint32_t touched = 0, bad = 0;
@@ -178,14 +178,21 @@ __device__ uint32_t ssa_tet(const ModelDev &m, const StepArgs &a, int32_t *cnt, 
     double dt_acc = 0.0;
     uint32_t j = 0;
     for (;;) {
-        float ar[kMaxReac];
+        // the attempt's two uniforms do not depend on the state: start them first
+        const uint4 w = philox4x32_10(a.key0, a.key1, c0, tet, j, (kPurposeReac << 28) | c3);
+        const float neg_log_u1 = -steps_logf(unit24f(w.x));
+        const float u2 = unit24f(w.y);
+        // propensities; psum[r] = a_0 + ... + a_r summed in reaction order
+        float psum[RM];
+        uint32_t pos = 0;
         float a0 = 0.0f;
 #pragma unroll
-        for (int r = 0; r < kMaxReac; ++r) {
-            ar[r] = 0.0f;
+        for (int r = 0; r < RM; ++r) {
             if (r < m.R) {
-                if ((active >> r) & 1u) ar[r] = propensity(m.reac[r], cnt, BLOCK, inv_nav);
-                a0 = __fadd_rn(a0, ar[r]);
+                const float ar = ((active >> r) & 1u) ? propensity(m.reac[r], cnt, BLOCK, inv_nav) : 0.0f;
+                a0 = __fadd_rn(a0, ar);
+                psum[r] = a0;
+                pos |= (ar > 0.0f ? 1u : 0u) << r;
             }
         }
         if (!(a0 > 0.0f)) break;
@@ -193,8 +200,7 @@ __device__ uint32_t ssa_tet(const ModelDev &m, const StepArgs &a, int32_t *cnt, 
             bad |= 2u;
             break;
         }
-        const uint4 w = philox4x32_10(a.key0, a.key1, c0, tet, j, (kPurposeReac << 28) | c3);
-        const float dt = __fdiv_rn(-steps_logf(unit24f(w.x)), a0);
+        const float dt = __fdiv_rn(neg_log_u1, a0);
         double dt_new;
         if (j == 0) {
             // 0 + (double)dt is exact, and (double)dt > tau_k <=> dt > tau_dn
@@ -205,21 +211,15 @@ __device__ uint32_t ssa_tet(const ModelDev &m, const StepArgs &a, int32_t *cnt, 
             if (dt_new > a.tau_k) break;
         }
         ++j;
-        const float target = __fmul_rn(unit24f(w.y), a0);
-        float c = 0.0f;
-        int pick = -1;
+        // first reaction whose running sum exceeds u2 a0 (running sums only grow,
+        // so the reactions past the target form a suffix); if none, the last
+        // reaction with a positive propensity
+        const float target = __fmul_rn(u2, a0);
+        uint32_t over = 0;
 #pragma unroll
-        for (int r = 0; r < kMaxReac; ++r) {
-            if (r < m.R && pick < 0) {
-                c = __fadd_rn(c, ar[r]);
-                if (c > target) pick = r;
-            }
-        }
-        if (pick < 0) {
-#pragma unroll
-            for (int r = kMaxReac - 1; r >= 0; --r)
-                if (r < m.R && pick < 0 && ar[r] > 0.0f) pick = r;
-        }
+        for (int r = 0; r < RM; ++r)
+            if (r < m.R) over |= (psum[r] > target ? 1u : 0u) << r;
+        const int pick = over ? __ffs(over) - 1 : (pos ? 31 - __clz(pos) : -1);
         if (pick < 0) break;
         dt_acc = dt_new;
         const ReacDesc &d = m.reac[pick];
@@ -292,6 +292,127 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *o
     return total;
 }
 
+// Trial molecules of one tet that draw words: every diffusive species with a
+// non-zero leave threshold keeps its trial count, the others get 0 (written
+// back to trial[s * stride]). Returns their sum, the tet's word count.
+__device__ __forceinline__ uint32_t trial_words(const ModelDev &m, const StepArgs &a, const uint4 A, int32_t *trial,
+                                                int stride) {
+    uint32_t W = 0;
+    for (int s = 0; s < m.S; ++s) {
+        int32_t M = 0;
+        if ((m.diffusive >> s) & 1u) {
+            M = trial[s * stride];
+            if ((uint32_t)(((uint64_t)A.w * a.scale[s]) >> 31) == 0u) M = 0;
+        }
+        trial[s * stride] = M;
+        W += (uint32_t)M;
+    }
+    return W;
+}
+
+// Work items per block the item map holds (beyond it, items find their tet
+// and species by search).
+template <int BLOCK>
+struct ItemMap {
+    static constexpr uint32_t kCap = 4 * BLOCK;
+};
+
+// Fill the item map for this thread's tet t: item blk_start[t] + k covers
+// words [k kItemWords, (k+1) kItemWords) of the tet's stream; record the tet,
+// the species of the item's first word and the number of the tet's trial
+// molecules before that species.
+template <int BLOCK>
+__device__ __forceinline__ void map_items(int t, uint32_t W, uint32_t first, uint32_t total, const int32_t *trial,
+                                          uint32_t *owner, uint32_t *before) {
+    if (W == 0 || total > ItemMap<BLOCK>::kCap) return;
+    const uint32_t n = (W + kItemWords - 1u) / kItemWords;
+    int s = 0;
+    uint32_t pre = 0, end = (uint32_t)trial[0];
+    for (uint32_t k = 0; k < n; ++k) {
+        const uint32_t w = k * kItemWords;
+        while (w >= end) {
+            pre = end;
+            ++s;
+            end += (uint32_t)trial[s * BLOCK];
+        }
+        owner[first + k] = (uint32_t)t | ((uint32_t)s << 9) | (k << 14);
+        before[first + k] = pre;
+    }
+}
+
+// One work item of the diffusion operator: up to kItemWords consecutive words
+// of one tet's stream (two Philox blocks), each deciding one trial molecule:
+// face f when T_{f-1} <= x < T_f (cumulative thresholds), stay when x >= T_3.
+// A mover is added to the neighbour's entry of nxt and removed from this tet's
+// shared count.
+template <int BLOCK>
+__device__ __forceinline__ void diffuse_item(const StepArgs &a, uint32_t item, uint32_t total, int nlive,
+                                             const uint32_t *blk_start, const uint32_t *owner,
+                                             const uint32_t *before, const uint32_t *words,
+                                             const int32_t *trial_all, int32_t *cnt_all, const uint4 *s_thr,
+                                             const int4 *s_nbr, const uint32_t *s_tet, uint32_t c0, uint32_t c3) {
+    int t, s;
+    uint32_t w, end;
+    if (total <= ItemMap<BLOCK>::kCap) {
+        const uint32_t o = owner[item];
+        t = (int)(o & 0x1FFu);
+        s = (int)((o >> 9) & 0x1Fu);
+        w = (o >> 14) * kItemWords;
+        end = before[item] + (uint32_t)trial_all[s * BLOCK + t];
+    } else {
+        // the tet owning this item: last t with blk_start[t] <= item
+        int lo = 0, hi = nlive - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (blk_start[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        t = lo;
+        w = (item - blk_start[t]) * kItemWords;
+        s = 0;
+        end = (uint32_t)trial_all[t];
+        while (w >= end) {
+            ++s;
+            end += (uint32_t)trial_all[s * BLOCK + t];
+        }
+    }
+    const int32_t *trial = trial_all + t;
+    const uint32_t Wt = words[t];
+    const uint32_t tet = s_tet[t];
+    const uint4 A = s_thr[t];
+    const int4 nb = s_nbr[t];
+    const size_t Tpad = (size_t)a.Tpad;
+    // both Philox blocks of the item as independent chains (the second may go unused)
+    const uint4 rw0 = philox4x32_10(a.key0, a.key1, c0, tet, w >> 2, (kPurposeDiff << 28) | c3);
+    const uint4 rw1 = philox4x32_10(a.key0, a.key1, c0, tet, (w >> 2) + 1u, (kPurposeDiff << 28) | c3);
+    uint64_t R = a.scale[s];
+    uint32_t T0 = (uint32_t)(((uint64_t)A.x * R) >> 31), T1 = (uint32_t)(((uint64_t)A.y * R) >> 31);
+    uint32_t T2 = (uint32_t)(((uint64_t)A.z * R) >> 31), T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (w < Wt) {
+            if (w >= end) {  // next species with trial molecules
+                do {
+                    ++s;
+                    end += (uint32_t)trial[s * BLOCK];
+                } while (w >= end);
+                R = a.scale[s];
+                T0 = (uint32_t)(((uint64_t)A.x * R) >> 31);
+                T1 = (uint32_t)(((uint64_t)A.y * R) >> 31);
+                T2 = (uint32_t)(((uint64_t)A.z * R) >> 31);
+                T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
+            }
+            const uint32_t x = word_of(k < 4 ? rw0 : rw1, k & 3) >> 1;
+            if (x < T3) {
+                const int nbr = x < T0 ? nb.x : x < T1 ? nb.y : x < T2 ? nb.z : nb.w;
+                atomicAdd(a.nxt + s * Tpad + nbr, 1);
+                atomicSub(&cnt_all[s * BLOCK + t], 1);
+            }
+            ++w;
+        }
+    }
+}
+
 // One diffusion window for BLOCK consecutive tets (device order).
 //  load   counts into shared memory; mobile entries of `cur` are zeroed as read
 //  A      each thread: its tet's propensities and first waiting time, in float;
@@ -302,7 +423,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *o
 //         spread evenly over the threads; each word moves or keeps one trial
 //         molecule; movers are added to the neighbour in `nxt` at once
 //  D      what stays is added to the tet's own entry of `nxt` (coalesced)
-template <int BLOCK>
+template <int BLOCK, int RM>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2) step_kernel(const __grid_constant__ ModelDev m,
                                                      const __grid_constant__ StepArgs a) {
     extern __shared__ __align__(16) int32_t smem[];  // cnt [S][BLOCK], trial [S][BLOCK]
@@ -316,6 +437,10 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2) step_kernel(const __g
     __shared__ uint32_t words[BLOCK];
     __shared__ uint32_t warp_tot[BLOCK / 32];
     __shared__ int32_t nqueue;
+    __shared__ uint8_t reacted[BLOCK];  // 1 = queued for the full SSA
+    __shared__ uint32_t next_item;
+    __shared__ uint32_t item_owner[ItemMap<BLOCK>::kCap];
+    __shared__ uint32_t item_before[ItemMap<BLOCK>::kCap];
     __shared__ __align__(8) uint64_t bar;
 
     const int S = m.S;
@@ -353,6 +478,7 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2) step_kernel(const __g
     }
     if (!a.orig) s_tet[tid] = (uint32_t)i;
     if (!a.rmask) s_mask[tid] = 0xFFFFFFFFu;
+    reacted[tid] = 0;
     const bool arrived = mbar_wait_bounded(&bar, 0);
     if (__syncthreads_or(!arrived)) {
         // the copies did not land in time: report, let them finish (bounded), skip the window
@@ -378,101 +504,68 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2) step_kernel(const __g
         const float inv_nav = s_inv_nav[tid];
         const uint32_t active = s_mask[tid];
         const int32_t *cnt = cnt_all + tid;
+        const uint4 w = philox4x32_10(a.key0, a.key1, c0, s_tet[tid], 0u, (kPurposeReac << 28) | c3);
+        const float neg_log_u1 = -steps_logf(unit24f(w.x));
         float a0 = 0.0f;
 #pragma unroll
-        for (int r = 0; r < kMaxReac; ++r) {
+        for (int r = 0; r < RM; ++r) {
             if (r < m.R) {
                 const float ar = ((active >> r) & 1u) ? propensity(m.reac[r], cnt, BLOCK, inv_nav) : 0.0f;
                 a0 = __fadd_rn(a0, ar);
             }
         }
         if (a0 > 0.0f) {
-            const uint4 w = philox4x32_10(a.key0, a.key1, c0, s_tet[tid], 0u, (kPurposeReac << 28) | c3);
-            const float dt = __fdiv_rn(-steps_logf(unit24f(w.x)), a0);
-            if (!(dt > a.tau_dn)) queue[atomicAdd(&nqueue, 1)] = tid;
-        }
-    }
-    __syncthreads();
-
-    // ---- B: full SSA of the tets that react, packed onto the first threads
-    for (int q = tid; q < nqueue; q += BLOCK) {
-        const int t = queue[q];
-        bad |= ssa_tet<BLOCK>(m, a, cnt_all + t, trial_all + t, s_tet[t], c0, c3, s_inv_nav[t], s_mask[t]);
-    }
-    __syncthreads();
-
-    // ---- C: trial molecules of the whole block, four words per work item
-    uint32_t W = 0;
-    if (live) {
-        const uint4 A = s_thr[tid];
-        for (int s = 0; s < S; ++s) {
-            int32_t M = 0;
-            if ((m.diffusive >> s) & 1u) {
-                M = trial_all[s * BLOCK + tid];
-                if ((uint32_t)(((uint64_t)A.w * a.scale[s]) >> 31) == 0u) M = 0;
+            const float dt = __fdiv_rn(neg_log_u1, a0);
+            if (!(dt > a.tau_dn)) {
+                queue[atomicAdd(&nqueue, 1)] = tid;
+                reacted[tid] = 1;
             }
-            trial_all[s * BLOCK + tid] = M;
-            W += (uint32_t)M;
         }
     }
+    __syncthreads();
+
+    // ---- C1 + B: the tets that did not react already have their trial counts
+    // (their counts); their work items are grabbed by every warp while the
+    // first warps run the full SSA of the tets that did (B), then join in.
+    uint32_t W = (live && !reacted[tid]) ? trial_words(m, a, s_thr[tid], trial_all + tid, BLOCK) : 0u;
     words[tid] = W;
-    const uint32_t total = block_exclusive_scan<BLOCK>((W + kItemWords - 1u) / kItemWords, blk_start, warp_tot);
-    if (tid == 0) blk_start[BLOCK] = total;
+    uint32_t total = block_exclusive_scan<BLOCK>((W + kItemWords - 1u) / kItemWords, blk_start, warp_tot);
+    if (tid == 0) {
+        blk_start[BLOCK] = total;
+        next_item = 0;
+    }
+    map_items<BLOCK>(tid, W, blk_start[tid], total, trial_all + tid, item_owner, item_before);
     __syncthreads();
-    for (uint32_t item = tid; item < total; item += BLOCK) {
-        // the tet owning this item: last t with blk_start[t] <= item
-        int lo = 0, hi = nlive - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (blk_start[mid] <= item) lo = mid;
-            else hi = mid - 1;
-        }
-        const int t = lo;
-        const uint32_t Wt = words[t];
-        const uint32_t tet = s_tet[t];
-        const uint4 A = s_thr[t];
-        const int4 nb = s_nbr[t];
-        const int32_t *trial = trial_all + t;
-        // species of the item's first word
-        uint32_t w = (item - blk_start[t]) * kItemWords;
-        int s = 0;
-        uint32_t end = (uint32_t)trial[0];
-        while (w >= end) {
-            ++s;
-            end += (uint32_t)trial[s * BLOCK];
-        }
-        uint64_t R = a.scale[s];
-        uint32_t T0 = (uint32_t)(((uint64_t)A.x * R) >> 31), T1 = (uint32_t)(((uint64_t)A.y * R) >> 31);
-        uint32_t T2 = (uint32_t)(((uint64_t)A.z * R) >> 31), T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
-#pragma unroll 1
-        for (int half = 0; half < kItemWords / 4 && w < Wt; ++half) {
-            const uint4 rw = philox4x32_10(a.key0, a.key1, c0, tet, w >> 2, (kPurposeDiff << 28) | c3);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (w < Wt) {
-                    if (w >= end) {  // next species with trial molecules
-                        do {
-                            ++s;
-                            end += (uint32_t)trial[s * BLOCK];
-                        } while (w >= end);
-                        R = a.scale[s];
-                        T0 = (uint32_t)(((uint64_t)A.x * R) >> 31);
-                        T1 = (uint32_t)(((uint64_t)A.y * R) >> 31);
-                        T2 = (uint32_t)(((uint64_t)A.z * R) >> 31);
-                        T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
-                    }
-                    // face f when T_{f-1} <= x < T_f (cumulative thresholds), stay when x >= T3
-                    const uint32_t x = word_of(rw, k) >> 1;
-                    if (x < T3) {
-                        const int nbr = x < T0 ? nb.x : x < T1 ? nb.y : x < T2 ? nb.z : nb.w;
-                        atomicAdd(a.nxt + s * Tpad + nbr, 1);
-                        atomicSub(&cnt_all[s * BLOCK + t], 1);
-                    }
-                    ++w;
-                }
-            }
+    const int nq = nqueue;
+    if (tid < nq) {
+        const int t = queue[tid];
+        bad |= ssa_tet<BLOCK, RM>(m, a, cnt_all + t, trial_all + t, s_tet[t], c0, c3, s_inv_nav[t], s_mask[t]);
+    }
+    __syncwarp();
+    {
+        const int lane = tid & 31;
+        for (;;) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&next_item, 32u);
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (base >= total) break;
+            const uint32_t item = base + (uint32_t)lane;
+            if (item < total)
+                diffuse_item<BLOCK>(a, item, total, nlive, blk_start, item_owner, item_before, words, trial_all,
+                                    cnt_all, s_thr, s_nbr, s_tet, c0, c3);
         }
     }
+    __syncthreads();
+    // ---- C2: the work items of the tets that reacted, now that their trial counts are known
+    W = (live && reacted[tid]) ? trial_words(m, a, s_thr[tid], trial_all + tid, BLOCK) : 0u;
+    words[tid] = W;
+    total = block_exclusive_scan<BLOCK>((W + kItemWords - 1u) / kItemWords, blk_start, warp_tot);
+    if (tid == 0) blk_start[BLOCK] = total;
+    map_items<BLOCK>(tid, W, blk_start[tid], total, trial_all + tid, item_owner, item_before);
+    __syncthreads();
+    for (uint32_t item = tid; item < total; item += BLOCK)
+        diffuse_item<BLOCK>(a, item, total, nlive, blk_start, item_owner, item_before, words, trial_all, cnt_all,
+                            s_thr, s_nbr, s_tet, c0, c3);
     __syncthreads();
 
     // ---- D: the molecules that stay (immobile species: written by this tet alone)
@@ -505,23 +598,23 @@ __global__ void logf_test_kernel(const float *x, int64_t n, float *out) {
 
 __global__ void add_u64_kernel(uint64_t *p, uint64_t v) { *p += v; }
 
-template <int BLOCK>
+template <int BLOCK, int RM>
 int launch_step_t(const ModelDev &m, const StepArgs &a, void *stream) {
     const int64_t grid = (a.T + BLOCK - 1) / BLOCK;
     const size_t smem = 2 * (size_t)m.S * BLOCK * sizeof(int32_t);
     static size_t static_smem = [] {
         cudaFuncAttributes fa{};
-        return cudaFuncGetAttributes(&fa, step_kernel<BLOCK>) == cudaSuccess ? fa.sharedSizeBytes : (size_t)0;
+        return cudaFuncGetAttributes(&fa, step_kernel<BLOCK, RM>) == cudaSuccess ? fa.sharedSizeBytes : (size_t)0;
     }();
     if (smem + static_smem > 48 * 1024) {  // opt in to more than the default 48 KB per block
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<BLOCK, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) {
             set_error(std::string("step kernel shared memory: ") + cudaGetErrorString(e));
             return STEPS_ERR_CUDA;
         }
     }
-    step_kernel<BLOCK><<<(unsigned)grid, BLOCK, smem, (cudaStream_t)stream>>>(m, a);
+    step_kernel<BLOCK, RM><<<(unsigned)grid, BLOCK, smem, (cudaStream_t)stream>>>(m, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error(std::string("step kernel launch: ") + cudaGetErrorString(e));
@@ -530,15 +623,24 @@ int launch_step_t(const ModelDev &m, const StepArgs &a, void *stream) {
     return STEPS_OK;
 }
 
+// reaction loops are unrolled to the smallest bucket of 8, 16, 24 or 32 that holds the model
+template <int BLOCK>
+int launch_step_b(const ModelDev &m, const StepArgs &a, void *stream) {
+    if (m.R <= 8) return launch_step_t<BLOCK, 8>(m, a, stream);
+    if (m.R <= 16) return launch_step_t<BLOCK, 16>(m, a, stream);
+    if (m.R <= 24) return launch_step_t<BLOCK, 24>(m, a, stream);
+    return launch_step_t<BLOCK, 32>(m, a, stream);
+}
+
 }  // namespace
 
 int launch_step(const ModelDev &m, const StepArgs &a, int block, void *stream) {
     if (a.T <= 0) return STEPS_OK;
     switch (block) {
-    case 64: return launch_step_t<64>(m, a, stream);
-    case 128: return launch_step_t<128>(m, a, stream);
-    case 512: return launch_step_t<512>(m, a, stream);
-    default: return launch_step_t<256>(m, a, stream);
+    case 64: return launch_step_b<64>(m, a, stream);
+    case 128: return launch_step_b<128>(m, a, stream);
+    case 512: return launch_step_b<512>(m, a, stream);
+    default: return launch_step_b<256>(m, a, stream);
     }
 }
 
