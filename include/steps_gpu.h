@@ -152,6 +152,50 @@ int steps_get_tau(const steps_sim *sim, double *tau);
 /* Windows run so far (the RNG window index) and kernel launches issued. */
 int steps_get_windows(const steps_sim *sim, uint64_t *windows, uint64_t *launches);
 
+/* ---------------------------------------------------------------------- */
+/* Batched form: one launch per window advances many simulations.         */
+/* ---------------------------------------------------------------------- */
+typedef struct steps_batch steps_batch;
+
+typedef struct steps_batch_options {
+    int32_t block;       /* threads per block; 0 = autotune over 128/256/512 on the first run (default) */
+    int32_t use_graph;   /* 1 = replay windows from a captured CUDA graph (default) */
+    int32_t reserved[6]; /* set to 0 */
+} steps_batch_options;
+
+void steps_batch_options_default(steps_batch_options *opt);
+
+/*
+ * A batch of n existing simulations (independent replicates or different
+ * meshes, seeds, time windows and models, on the current device). Each
+ * window launch covers every member's tiles; a member's model and window
+ * arguments are read from a device table, and its window counter and buffer
+ * parity advance on the device, so the whole step loop replays from a CUDA
+ * graph. Results are the same bits as running each member alone with
+ * steps_run (the random numbers are addressed by member seed, window and
+ * original tet). The batch does not own the members: they must outlive it,
+ * and must not be run or changed by other calls while a batch call runs.
+ * cuda_stream: stream of the batch's launches (NULL = legacy default stream).
+ */
+int steps_batch_create(steps_sim *const *members, int32_t n, const steps_batch_options *opt, void *cuda_stream,
+                       steps_batch **out);
+void steps_batch_destroy(steps_batch *batch);
+
+/*
+ * Advance member j to t_end[j] (absolute seconds, [n] host array) by the
+ * window rule of steps_run: full windows of the member's own tau, then a
+ * shortened last window where time remains. Members with fewer windows sit
+ * out the later launches. With block autotuning, the first run times three
+ * windows at each candidate block size (real windows: results do not depend
+ * on the block size) and keeps the fastest. Synchronises with the batch's
+ * stream once. Errors as steps_run.
+ */
+int steps_batch_run(steps_batch *batch, const double *t_end);
+
+/* Block size in use, kernel launches issued so far, and the autotuner's
+ * milliseconds per window for blocks 128/256/512 (tune_ms[3], zeros if not run). */
+int steps_batch_info(const steps_batch *batch, int32_t *block, uint64_t *launches, float *tune_ms);
+
 /*
  * Advance `sim` to t_end on counts held in a caller-owned device buffer,
  * without allocating any memory. The paper has no counterpart: this serves

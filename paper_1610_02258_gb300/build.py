@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libsteps_gpu.so")
-SOURCES = ["steps_host.cpp", "steps_kernels.cu", "steps_api.cu"]
+SOURCES = ["steps_host.cpp", "steps_kernels.cu", "steps_batch.cu", "steps_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

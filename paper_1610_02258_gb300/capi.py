@@ -29,6 +29,8 @@ EXPORTS = [
     "steps_set_counts", "steps_get_counts", "steps_set_counts_all", "steps_get_counts_all",
     "steps_set_reac_mask", "steps_run", "steps_get_time", "steps_get_tau", "steps_get_windows",
     "steps_last_error", "steps_debug_philox", "steps_debug_logf", "steps_run_noalloc",
+    "steps_batch_options_default", "steps_batch_create", "steps_batch_destroy", "steps_batch_run",
+    "steps_batch_info",
 ]
 
 
@@ -41,6 +43,10 @@ class StepsError(RuntimeError):
 class steps_options(ctypes.Structure):
     _fields_ = [("occupancy", ctypes.c_int32), ("reorder", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class steps_batch_options(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 def _load():
@@ -71,6 +77,12 @@ def _load():
         "steps_debug_philox": (ctypes.c_int, [u64, P, i64, P]),
         "steps_debug_logf": (ctypes.c_int, [P, i64, P]),
         "steps_run_noalloc": (ctypes.c_int, [P, P, ctypes.c_double]),
+        "steps_batch_options_default": (None, [ctypes.POINTER(steps_batch_options)]),
+        "steps_batch_create": (ctypes.c_int, [P, i32, ctypes.POINTER(steps_batch_options), P, PP]),
+        "steps_batch_destroy": (None, [P]),
+        "steps_batch_run": (ctypes.c_int, [P, P]),
+        "steps_batch_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint64),
+                                            ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -215,6 +227,64 @@ def steps_debug_logf(x):
     out = np.empty_like(a)
     _check(lib.steps_debug_logf(_ptr(a), a.size, _ptr(out)))
     return out
+
+
+def steps_batch_options_default():
+    o = steps_batch_options()
+    lib.steps_batch_options_default(ctypes.byref(o))
+    return o
+
+
+def steps_batch_create(sim_handles, opt=None, cuda_stream=None):
+    arr = (ctypes.c_void_p * len(sim_handles))(*[h.value for h in sim_handles])
+    h = ctypes.c_void_p()
+    _check(lib.steps_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(sim_handles),
+                                  ctypes.byref(opt) if opt is not None else None,
+                                  ctypes.c_void_p(cuda_stream) if cuda_stream else None, ctypes.byref(h)))
+    return h
+
+
+def steps_batch_destroy(h):
+    lib.steps_batch_destroy(h)
+
+
+def steps_batch_run(batch, t_end):
+    t = np.ascontiguousarray(t_end, np.float64)
+    _check(lib.steps_batch_run(batch, _ptr(t)))
+
+
+def steps_batch_info(batch):
+    b, l = ctypes.c_int32(), ctypes.c_uint64()
+    tm = (ctypes.c_float * 3)()
+    _check(lib.steps_batch_info(batch, ctypes.byref(b), ctypes.byref(l), tm))
+    return b.value, l.value, list(tm)
+
+
+class Batch:
+    """A batch over existing Simulation objects (kept alive by this object)."""
+
+    def __init__(self, sims, block=0, use_graph=True, cuda_stream=None):
+        self.sims = list(sims)
+        opt = steps_batch_options_default()
+        opt.block = block
+        opt.use_graph = 1 if use_graph else 0
+        self._h = steps_batch_create([s._sim for s in self.sims], opt, cuda_stream)
+
+    def run(self, t_end):
+        t = np.broadcast_to(np.asarray(t_end, np.float64), (len(self.sims),))
+        steps_batch_run(self._h, t)
+
+    @property
+    def info(self):
+        return steps_batch_info(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            steps_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 class Simulation:

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <algorithm>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -569,6 +570,327 @@ int steps_debug_logf(const float *x, int64_t n, float *out) {
     cudaFree(dx);
     cudaFree(dout);
     return rc;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched form: one launch per window over many simulations.
+// ---------------------------------------------------------------------------
+struct steps_batch {
+    std::vector<steps_sim *> members;
+    cudaStream_t stream = nullptr;
+    int block = 256;
+    bool autotune = false;
+    bool use_graph = true;
+    int max_S = 1, max_R = 0;
+    RepEntry *h_reps = nullptr;  // pinned host mirror
+    RepEntry *d_reps = nullptr;
+    uint32_t *d_err = nullptr;
+    struct Work {
+        BlockWork *d = nullptr;
+        int64_t n = 0;
+        cudaGraphExec_t graph = nullptr;
+    };
+    Work work[4];  // block sizes 64, 128, 256, 512
+    uint64_t launches = 0;
+    std::vector<float> tune_ms;  // autotune timings per candidate block (ms per window)
+
+    static int slot(int b) { return b == 64 ? 0 : b == 128 ? 1 : b == 512 ? 3 : 2; }
+
+    ~steps_batch() {
+        for (auto &w : work) {
+            if (w.graph) cudaGraphExecDestroy(w.graph);
+            cudaFree(w.d);
+        }
+        cudaFree(d_reps);
+        cudaFree(d_err);
+        cudaFreeHost(h_reps);
+    }
+
+    int build_work(int b) {
+        Work &w = work[slot(b)];
+        if (w.d) return STEPS_OK;
+        std::vector<BlockWork> v;
+        for (size_t j = 0; j < members.size(); ++j) {
+            const int64_t tiles = (members[j]->T + b - 1) / b;
+            for (int64_t t = 0; t < tiles; ++t) v.push_back(BlockWork{(int32_t)j, (int32_t)t});
+        }
+        w.n = (int64_t)v.size();
+        if (w.n == 0) return STEPS_OK;
+        if (!cuda_ok(cudaMalloc((void **)&w.d, v.size() * sizeof(BlockWork)), "steps_batch: alloc work"))
+            return STEPS_ERR_OOM;
+        if (!cuda_ok(cudaMemcpy(w.d, v.data(), v.size() * sizeof(BlockWork), cudaMemcpyHostToDevice),
+                     "steps_batch: upload work"))
+            return STEPS_ERR_CUDA;
+        return STEPS_OK;
+    }
+
+    int window(int b, cudaStream_t st) {  // one batched window + advance
+        Work &w = work[slot(b)];
+        int rc = launch_step_batch(w.d, w.n, d_reps, max_S, max_R, b, st);
+        if (!rc) rc = launch_advance(d_reps, (int32_t)members.size(), st);
+        launches += 2;
+        return rc;
+    }
+
+    int graph_for(int b) {
+        Work &w = work[slot(b)];
+        if (w.graph) return STEPS_OK;
+        cudaStream_t cs = nullptr;
+        if (!cuda_ok(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate")) return STEPS_ERR_CUDA;
+        cudaGraph_t g = nullptr;
+        int rc = STEPS_OK;
+        if (!cuda_ok(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture")) {
+            cudaStreamDestroy(cs);
+            return STEPS_ERR_CUDA;
+        }
+        const uint64_t before = launches;
+        for (int q = 0; q < kGraphWindows && rc == STEPS_OK; ++q) rc = window(b, cs);
+        launches = before;
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (rc == STEPS_OK && !cuda_ok(e, "cudaStreamEndCapture")) rc = STEPS_ERR_CUDA;
+        if (rc == STEPS_OK && !cuda_ok(cudaGraphInstantiate(&w.graph, g, 0), "cudaGraphInstantiate")) rc = STEPS_ERR_CUDA;
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        return rc;
+    }
+
+    int run_windows(int b, int64_t n) {  // n windows at block size b
+        int rc = build_work(b);
+        if (rc) return rc;
+        int64_t done = 0;
+        if (use_graph && n >= kGraphWindows) {
+            rc = graph_for(b);
+            if (rc) return rc;
+            for (; n - done >= kGraphWindows; done += kGraphWindows) {
+                if (!cuda_ok(cudaGraphLaunch(work[slot(b)].graph, stream), "cudaGraphLaunch")) return STEPS_ERR_CUDA;
+                launches += 2 * kGraphWindows;
+            }
+        }
+        for (; done < n; ++done) {
+            rc = window(b, stream);
+            if (rc) return rc;
+        }
+        return STEPS_OK;
+    }
+};
+
+extern "C" {
+
+void steps_batch_options_default(steps_batch_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->block = 0;
+    opt->use_graph = 1;
+}
+
+int steps_batch_create(steps_sim *const *members, int32_t n, const steps_batch_options *opt, void *cuda_stream,
+                       steps_batch **out) {
+    CHECK_NULL(out, "steps_batch_create");
+    *out = nullptr;
+    CHECK_NULL(members, "steps_batch_create");
+    if (n < 1) {
+        set_error("steps_batch_create: need at least one member");
+        return STEPS_ERR_ARG;
+    }
+    std::unique_ptr<steps_batch> b(new (std::nothrow) steps_batch);
+    if (!b) return STEPS_ERR_OOM;
+    steps_batch_options o;
+    if (opt) o = *opt;
+    else steps_batch_options_default(&o);
+    if (o.block != 0 && o.block != 64 && o.block != 128 && o.block != 256 && o.block != 512) {
+        set_error("steps_batch_create: block must be 0 (autotune), 64, 128, 256 or 512");
+        return STEPS_ERR_ARG;
+    }
+    b->autotune = o.block == 0;
+    b->block = o.block == 0 ? 256 : o.block;
+    b->use_graph = o.use_graph != 0;
+    b->stream = (cudaStream_t)cuda_stream;
+    for (int32_t j = 0; j < n; ++j) {
+        if (!members[j]) {
+            set_error("steps_batch_create: NULL member");
+            return STEPS_ERR_ARG;
+        }
+        for (int32_t q = 0; q < j; ++q)
+            if (members[q] == members[j]) {
+                set_error("steps_batch_create: a simulation appears twice");
+                return STEPS_ERR_ARG;
+            }
+        b->members.push_back(members[j]);
+        b->max_S = std::max(b->max_S, members[j]->S);
+        b->max_R = std::max(b->max_R, members[j]->model.R);
+    }
+    if (!cuda_ok(cudaMallocHost((void **)&b->h_reps, sizeof(RepEntry) * n), "steps_batch_create: host alloc") ||
+        !cuda_ok(cudaMalloc((void **)&b->d_reps, sizeof(RepEntry) * n), "steps_batch_create: alloc") ||
+        !cuda_ok(cudaMalloc((void **)&b->d_err, 4), "steps_batch_create: alloc") ||
+        !cuda_ok(cudaMemset(b->d_err, 0, 4), "steps_batch_create: memset"))
+        return STEPS_ERR_OOM;
+    int rc = b->build_work(b->block);
+    if (rc) return rc;
+    *out = b.release();
+    return STEPS_OK;
+}
+
+void steps_batch_destroy(steps_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    delete b;
+}
+
+int steps_batch_run(steps_batch *b, const double *t_end) {
+    CHECK_NULL(b, "steps_batch_run");
+    CHECK_NULL(t_end, "steps_batch_run");
+    const size_t n = b->members.size();
+    for (size_t j = 0; j < n; ++j)
+        if (!std::isfinite(t_end[j])) {
+            set_error("steps_batch_run: t_end must be finite");
+            return STEPS_ERR_ARG;
+        }
+    // members' own streams may still hold work
+    for (steps_sim *m : b->members)
+        if (!cuda_ok(cudaStreamSynchronize(m->stream), "steps_batch_run: member stream")) return STEPS_ERR_CUDA;
+    // the window schedule of every member (the loop of steps_run)
+    std::vector<int64_t> nfull(n, 0);
+    std::vector<double> partial(n, 0.0);  // > 0: a shortened last window of this length
+    int64_t nmax = 0;
+    for (size_t j = 0; j < n; ++j) {
+        steps_sim *m = b->members[j];
+        const double tau = m->tab.tau;
+        const bool finite = std::isfinite(tau);
+        const double tol = finite ? 1e-9 * tau : 0.0;
+        int64_t k = 0;
+        for (;;) {
+            const int64_t kk = m->k_grid + k;
+            const double t = kk == 0 ? m->t_base : m->t_base + (double)kk * tau;
+            if (!(t_end[j] - t > tol)) break;
+            if (finite && t + tau <= t_end[j] + tol) {
+                ++k;
+            } else {
+                partial[j] = t_end[j] - t;
+                break;
+            }
+        }
+        nfull[j] = k;
+        nmax = std::max(nmax, k);
+    }
+    // table for the full windows
+    for (size_t j = 0; j < n; ++j) {
+        steps_sim *m = b->members[j];
+        RepEntry &e = b->h_reps[j];
+        std::memset(&e, 0, sizeof(e));
+        e.model = m->model.dev;
+        e.args = m->args(0, m->k_total, nullptr, std::isfinite(m->tab.tau) ? m->tab.tau : 1.0, m->scale_full);
+        e.args.err = b->d_err;
+        e.cnt[0] = m->d_cnt[0];
+        e.cnt[1] = m->d_cnt[1];
+        e.parity = (uint32_t)m->cur;
+        e.window_end = m->k_total + (uint64_t)nfull[j];
+    }
+    if (!cuda_ok(cudaMemcpyAsync(b->d_reps, b->h_reps, sizeof(RepEntry) * n, cudaMemcpyHostToDevice, b->stream),
+                 "steps_batch_run: upload"))
+        return STEPS_ERR_CUDA;
+    int64_t done = 0;
+    int rc = STEPS_OK;
+    if (b->autotune && nmax >= 12) {
+        // time 3 windows at each candidate block size, keep the fastest
+        const int cand[3] = {128, 256, 512};
+        b->tune_ms.assign(3, 0.f);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        int best_b = b->block;
+        for (int c = 0; c < 3 && rc == STEPS_OK; ++c) {
+            rc = b->build_work(cand[c]);
+            if (rc) break;
+            rc = b->run_windows(cand[c], 1);  // warm
+            cudaEventRecord(e0, b->stream);
+            if (!rc) rc = b->run_windows(cand[c], 3);
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            b->tune_ms[c] = ms / 3.f;
+            if (ms < best) {
+                best = ms;
+                best_b = cand[c];
+            }
+            done += 4;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+        b->block = best_b;
+        b->autotune = false;
+    }
+    rc = b->run_windows(b->block, nmax - done);
+    if (rc) return rc;
+    // shortened last windows
+    bool any_partial = false;
+    for (size_t j = 0; j < n; ++j) {
+        steps_sim *m = b->members[j];
+        RepEntry &e = b->h_reps[j];
+        const uint64_t w = m->k_total + (uint64_t)nfull[j];
+        e.args.window = w;
+        e.parity = (uint32_t)(m->cur ^ (int)(nfull[j] & 1));
+        e.window_end = w;
+        if (partial[j] > 0.0) {
+            any_partial = true;
+            uint32_t scale[kMaxSpecies] = {};
+            for (int s = 0; s < m->S; ++s) scale[s] = species_scale(m->model, m->tab, s, partial[j]);
+            StepArgs a = m->args(0, w, nullptr, partial[j], scale);
+            a.err = b->d_err;
+            e.args = a;
+            e.window_end = w + 1;
+        }
+    }
+    if (any_partial) {
+        if (!cuda_ok(cudaMemcpyAsync(b->d_reps, b->h_reps, sizeof(RepEntry) * n, cudaMemcpyHostToDevice, b->stream),
+                     "steps_batch_run: upload"))
+            return STEPS_ERR_CUDA;
+        rc = b->run_windows(b->block, 1);
+        if (rc) return rc;
+    }
+    // members' clocks and buffers
+    for (size_t j = 0; j < n; ++j) {
+        steps_sim *m = b->members[j];
+        const int64_t wins = nfull[j] + (partial[j] > 0.0 ? 1 : 0);
+        m->k_total += (uint64_t)wins;
+        m->launches += (uint64_t)wins;
+        m->cur ^= (int)(wins & 1);
+        if (partial[j] > 0.0) {
+            m->t_base = t_end[j];
+            m->k_grid = 0;
+        } else {
+            m->k_grid += nfull[j];
+        }
+    }
+    uint32_t err = 0;
+    if (!cuda_ok(cudaMemcpyAsync(&err, b->d_err, 4, cudaMemcpyDeviceToHost, b->stream), "steps_batch_run: error word") ||
+        !cuda_ok(cudaStreamSynchronize(b->stream), "steps_batch_run"))
+        return STEPS_ERR_CUDA;
+    if (err) {
+        cudaMemset(b->d_err, 0, 4);
+        if (err & 4u) {
+            set_error("steps_batch_run: a bulk copy into shared memory did not complete within its wait limit");
+            return STEPS_ERR_TIMEOUT;
+        }
+        set_error(err & 2u ? "steps_batch_run: a tet fired more than 2^24 reactions in one window"
+                           : "steps_batch_run: a negative count was seen on the device");
+        return STEPS_ERR_STATE;
+    }
+    return STEPS_OK;
+}
+
+int steps_batch_info(const steps_batch *b, int32_t *block, uint64_t *launches, float *tune_ms) {
+    CHECK_NULL(b, "steps_batch_info");
+    if (block) *block = b->block;
+    if (launches) *launches = b->launches;
+    if (tune_ms)
+        for (int c = 0; c < 3; ++c) tune_ms[c] = c < (int)b->tune_ms.size() ? b->tune_ms[c] : 0.f;
+    return STEPS_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,101 @@
+// Batched step kernel: one launch runs a window for many simulations (members
+// of different sizes, seeds, time windows and models). Each block reads its
+// member's model and arguments from a device table into shared memory, then
+// runs the same tile body as the plain kernel; a small kernel advances every
+// member's window counter and buffer parity on the device, so that the whole
+// step loop can be replayed from a CUDA graph.
+#include "steps_step.cuh"
+
+namespace steps {
+
+namespace {
+
+template <int BLOCK, int RM>
+__global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2)
+    step_kernel_batch(const BlockWork *__restrict__ work, const RepEntry *__restrict__ reps) {
+    __shared__ __align__(16) ModelDev t_model;
+    __shared__ __align__(16) StepArgs t_args;
+    __shared__ int32_t t_tile;
+    const BlockWork bw = work[blockIdx.x];
+    const RepEntry *e = reps + bw.rep;
+    if (e->args.window >= e->window_end) return;  // member idle in this launch (block-uniform)
+    static_assert(sizeof(ModelDev) % 4 == 0 && sizeof(StepArgs) % 4 == 0, "word copy");
+    const uint32_t *src_m = reinterpret_cast<const uint32_t *>(&e->model);
+    uint32_t *dst_m = reinterpret_cast<uint32_t *>(&t_model);
+    for (int k = threadIdx.x; k < (int)(sizeof(ModelDev) / 4); k += BLOCK) dst_m[k] = src_m[k];
+    const uint32_t *src_a = reinterpret_cast<const uint32_t *>(&e->args);
+    uint32_t *dst_a = reinterpret_cast<uint32_t *>(&t_args);
+    for (int k = threadIdx.x; k < (int)(sizeof(StepArgs) / 4); k += BLOCK) dst_a[k] = src_a[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        t_args.cur = e->cnt[e->parity];
+        t_args.nxt = e->cnt[e->parity ^ 1u];
+        t_tile = bw.tile;
+    }
+    __syncthreads();
+    step_tile<BLOCK, RM>(t_model, t_args, (int64_t)t_tile);
+}
+
+template <int BLOCK, int RM>
+int launch_batch_t(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, void *stream) {
+    const size_t smem = 2 * (size_t)max_S * BLOCK * sizeof(int32_t);
+    static size_t static_smem = [] {
+        cudaFuncAttributes fa{};
+        return cudaFuncGetAttributes(&fa, step_kernel_batch<BLOCK, RM>) == cudaSuccess ? fa.sharedSizeBytes
+                                                                                        : (size_t)0;
+    }();
+    if (smem + static_smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel_batch<BLOCK, RM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            set_error(std::string("batched step kernel shared memory: ") + cudaGetErrorString(e));
+            return STEPS_ERR_CUDA;
+        }
+    }
+    step_kernel_batch<BLOCK, RM><<<(unsigned)nblocks, BLOCK, smem, (cudaStream_t)stream>>>(work, reps);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("batched step kernel launch: ") + cudaGetErrorString(e));
+        return STEPS_ERR_CUDA;
+    }
+    return STEPS_OK;
+}
+
+template <int BLOCK>
+int launch_batch_b(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R, void *stream) {
+    if (max_R <= 8) return launch_batch_t<BLOCK, 8>(work, nblocks, reps, max_S, stream);
+    if (max_R <= 16) return launch_batch_t<BLOCK, 16>(work, nblocks, reps, max_S, stream);
+    if (max_R <= 24) return launch_batch_t<BLOCK, 24>(work, nblocks, reps, max_S, stream);
+    return launch_batch_t<BLOCK, 32>(work, nblocks, reps, max_S, stream);
+}
+
+__global__ void advance_kernel(RepEntry *reps, int32_t n) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    RepEntry &e = reps[j];
+    if (e.args.window < e.window_end) {
+        e.args.window += 1;
+        e.parity ^= 1u;
+    }
+}
+
+}  // namespace
+
+int launch_step_batch(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R, int block,
+                      void *stream) {
+    if (nblocks <= 0) return STEPS_OK;
+    switch (block) {
+    case 64: return launch_batch_b<64>(work, nblocks, reps, max_S, max_R, stream);
+    case 128: return launch_batch_b<128>(work, nblocks, reps, max_S, max_R, stream);
+    case 512: return launch_batch_b<512>(work, nblocks, reps, max_S, max_R, stream);
+    default: return launch_batch_b<256>(work, nblocks, reps, max_S, max_R, stream);
+    }
+}
+
+int launch_advance(RepEntry *reps, int32_t n, void *stream) {
+    if (n <= 0) return STEPS_OK;
+    advance_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(reps, n);
+    return cudaGetLastError() == cudaSuccess ? STEPS_OK : STEPS_ERR_CUDA;
+}
+
+}  // namespace steps

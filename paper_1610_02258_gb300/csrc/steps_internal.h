@@ -67,6 +67,25 @@ struct StepArgs {
     uint32_t scale[kMaxSpecies];  // per-species fixed-point scale for this window length
 };
 
+// One member of a batched launch, resident in device memory. The step kernel
+// reads its member's model and arguments from here (cur/nxt chosen by
+// `parity`); the advance kernel moves `args.window` and `parity` after every
+// window while args.window < window_end.
+struct RepEntry {
+    ModelDev model;
+    StepArgs args;
+    int32_t *cnt[2];
+    uint32_t parity;
+    uint32_t pad_;
+    uint64_t window_end;
+};
+
+// A block of a batched launch: member index and tile (BLOCK consecutive tets) within it.
+struct BlockWork {
+    int32_t rep;
+    int32_t tile;
+};
+
 // ---------------------------------------------------------------- host objects
 struct HostMesh {
     int64_t nv = 0, nt = 0;
@@ -107,5 +126,8 @@ int launch_step(const ModelDev &m, const StepArgs &a, int block, void *stream);
 int launch_philox_test(uint64_t seed, const uint32_t *d_ctr, int64_t n, uint32_t *d_out, void *stream);
 int launch_logf_test(const float *d_x, int64_t n, float *d_out, void *stream);
 int launch_add_u64(uint64_t *p, uint64_t v, void *stream);
+int launch_step_batch(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R, int block,
+                      void *stream);
+int launch_advance(RepEntry *reps, int32_t n, void *stream);
 
 }  // namespace steps

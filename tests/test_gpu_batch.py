@@ -1,0 +1,70 @@
+"""GPU tests of the batched form: one launch per window over many
+simulations must give, for every member, exactly the counts, window count
+and clock of that member run alone with steps_run."""
+import numpy as np
+import pytest
+
+from paper_1610_02258_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_02258_gb300.build import build
+    build()
+    from paper_1610_02258_gb300 import capi as c
+    return c
+
+
+def _workloads():
+    ws = []
+    for j, nx in enumerate([3, 7, 1, 12, 5]):
+        ws.append(I.config2(seed=100 + j, nx=nx, t_end=3e-3 + 0.37e-3 * j))
+    ws.append(I.config1(seed=7))                                # another model (3 species, 2 reactions)
+    ws.append(I.config3(h=0.5e-6, t_end=0.15e-3))               # 20 species, masked influx
+    return ws
+
+
+@pytest.mark.parametrize("block,use_graph", [(0, True), (128, False), (512, True)])
+def test_batch_equals_members_alone(capi, block, use_graph):
+    ws = _workloads()
+    alone = []
+    for w in ws:
+        s = capi.from_workload(w)
+        s.run(w.t_end)
+        alone.append((s.get_counts(), s.windows, s.time))
+    members = [capi.from_workload(w) for w in ws]
+    b = capi.Batch(members, block=block, use_graph=use_graph)
+    b.run([w.t_end for w in ws])
+    for (ref, win, t), m in zip(alone, members):
+        assert m.windows == win and m.time == t
+        assert np.array_equal(m.get_counts(), ref)
+    blk, launches, tune = b.info
+    assert launches > 0
+    if block == 0:
+        assert blk in (128, 256, 512) and all(x > 0 for x in tune)
+    else:
+        assert blk == block
+
+
+def test_batch_resume_and_mixed_end_times(capi):
+    """Two batch runs in a row (second one ending off the window grid for some
+    members, on it for others) equal one run per member alone."""
+    ws = _workloads()[:4]
+    members = [capi.from_workload(w) for w in ws]
+    b = capi.Batch(members, block=256)
+    tau = [m.tau for m in members]
+    t1 = [5 * t for t in tau]
+    t2 = [w.t_end for w in ws]
+    b.run(t1)
+    b.run(t2)
+    for w, m, t1j in zip(ws, members, t1):
+        s = capi.from_workload(w)
+        s.run(t1j)
+        s.run(w.t_end)
+        assert m.windows == s.windows
+        assert np.array_equal(m.get_counts(), s.get_counts())
