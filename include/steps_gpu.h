@@ -119,6 +119,16 @@ int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t 
                      const steps_options *opt, void *cuda_stream, steps_sim **out);
 void steps_sim_destroy(steps_sim *sim);
 
+/*
+ * A new simulation with the mesh, model, options, region masks and device
+ * tables of `src` (copied on the device, no host-side rebuilding), its own
+ * seed and stream, zero counts and time 0. For serving many jobs that share
+ * a mesh and model.
+ */
+int steps_sim_clone(const steps_sim *src, uint64_t seed, void *cuda_stream, steps_sim **out);
+/* Device memory a simulation holds, in bytes (for admission by memory budget). */
+int steps_sim_device_bytes(const steps_sim *sim, int64_t *bytes);
+
 /* Counts of one species in every tet: counts[nt] int32 >= 0, original tet order (host). */
 int steps_set_counts(steps_sim *sim, int32_t species, const int32_t *counts);
 int steps_get_counts(const steps_sim *sim, int32_t species, int32_t *out);

@@ -30,7 +30,7 @@ EXPORTS = [
     "steps_set_reac_mask", "steps_run", "steps_get_time", "steps_get_tau", "steps_get_windows",
     "steps_last_error", "steps_debug_philox", "steps_debug_logf", "steps_run_noalloc",
     "steps_batch_options_default", "steps_batch_create", "steps_batch_destroy", "steps_batch_run",
-    "steps_batch_info",
+    "steps_batch_info", "steps_sim_clone", "steps_sim_device_bytes",
 ]
 
 
@@ -83,6 +83,8 @@ def _load():
         "steps_batch_run": (ctypes.c_int, [P, P]),
         "steps_batch_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint64),
                                             ctypes.POINTER(ctypes.c_float)]),
+        "steps_sim_clone": (ctypes.c_int, [P, u64, P, PP]),
+        "steps_sim_device_bytes": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -150,6 +152,19 @@ def steps_sim_create(mesh, model, seed, opt=None, cuda_stream=None):
     _check(lib.steps_sim_create(mesh, model, ctypes.c_uint64(seed), ctypes.byref(opt) if opt is not None else None,
                                 ctypes.c_void_p(cuda_stream) if cuda_stream else None, ctypes.byref(h)))
     return h
+
+
+def steps_sim_clone(src, seed, cuda_stream=None):
+    h = ctypes.c_void_p()
+    _check(lib.steps_sim_clone(src, ctypes.c_uint64(seed), ctypes.c_void_p(cuda_stream) if cuda_stream else None,
+                               ctypes.byref(h)))
+    return h
+
+
+def steps_sim_device_bytes(sim):
+    n = ctypes.c_int64()
+    _check(lib.steps_sim_device_bytes(sim, ctypes.byref(n)))
+    return n.value
 
 
 def steps_sim_destroy(h):
@@ -304,6 +319,20 @@ class Simulation:
         opt.block = block
         opt.use_graph = 1 if use_graph else 0
         self._sim = steps_sim_create(self._mesh, self._model, seed, opt, cuda_stream)
+
+    def clone(self, seed, cuda_stream=None):
+        """A new Simulation sharing this one's mesh, model and device tables
+        (copied on the device), with its own seed, zero counts, time 0."""
+        c = Simulation.__new__(Simulation)
+        c.S, c.R, c.nt = self.S, self.R, self.nt
+        c._mesh = None
+        c._model = None
+        c._sim = steps_sim_clone(self._sim, seed, cuda_stream)
+        return c
+
+    @property
+    def device_bytes(self):
+        return steps_sim_device_bytes(self._sim)
 
     def close(self):
         if getattr(self, "_sim", None):

@@ -361,6 +361,75 @@ int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t 
     return STEPS_OK;
 }
 
+int steps_sim_clone(const steps_sim *src, uint64_t seed, void *cuda_stream, steps_sim **out) {
+    CHECK_NULL(out, "steps_sim_clone");
+    *out = nullptr;
+    CHECK_NULL(src, "steps_sim_clone");
+    std::unique_ptr<steps_sim> s(new (std::nothrow) steps_sim);
+    if (!s) {
+        set_error("steps_sim_clone: out of host memory");
+        return STEPS_ERR_OOM;
+    }
+    s->model = src->model;
+    s->tab = src->tab;
+    s->opt = src->opt;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->T = src->T;
+    s->Tpad = src->Tpad;
+    s->S = src->S;
+    s->seed = seed;
+    s->h_rmask = src->h_rmask;
+    std::memcpy(s->scale_full, src->scale_full, sizeof(s->scale_full));
+    const size_t Tpad = (size_t)s->Tpad, S = (size_t)s->S, T = (size_t)s->T;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    alloc((void **)&s->d_cnt[0], S * Tpad * 4);
+    alloc((void **)&s->d_cnt[1], S * Tpad * 4);
+    alloc((void **)&s->d_nbr, Tpad * 16);
+    alloc((void **)&s->d_thr, Tpad * 16);
+    alloc((void **)&s->d_inv_nav, Tpad * 4);
+    alloc((void **)&s->d_err, 4);
+    alloc((void **)&s->d_window_base, 8);
+    alloc((void **)&s->d_stage, S * T * 4);
+    if (src->d_orig) {
+        alloc((void **)&s->d_orig, Tpad * 4);
+        alloc((void **)&s->d_inv_perm, T * 4);
+    }
+    if (src->d_rmask) alloc((void **)&s->d_rmask, Tpad * 4);
+    if (e != cudaSuccess) {
+        set_error(std::string("steps_sim_clone: device allocation failed: ") + cudaGetErrorString(e));
+        cudaGetLastError();
+        return STEPS_ERR_OOM;
+    }
+    cudaStream_t st = s->stream;
+    bool ok = cuda_ok(cudaMemcpyAsync(s->d_nbr, src->d_nbr, Tpad * 16, cudaMemcpyDeviceToDevice, st), "clone") &&
+              cuda_ok(cudaMemcpyAsync(s->d_thr, src->d_thr, Tpad * 16, cudaMemcpyDeviceToDevice, st), "clone") &&
+              cuda_ok(cudaMemcpyAsync(s->d_inv_nav, src->d_inv_nav, Tpad * 4, cudaMemcpyDeviceToDevice, st), "clone") &&
+              cuda_ok(cudaMemsetAsync(s->d_cnt[0], 0, S * Tpad * 4, st), "clone") &&
+              cuda_ok(cudaMemsetAsync(s->d_cnt[1], 0, S * Tpad * 4, st), "clone") &&
+              cuda_ok(cudaMemsetAsync(s->d_err, 0, 4, st), "clone") &&
+              cuda_ok(cudaMemsetAsync(s->d_window_base, 0, 8, st), "clone");
+    if (ok && src->d_orig)
+        ok = cuda_ok(cudaMemcpyAsync(s->d_orig, src->d_orig, Tpad * 4, cudaMemcpyDeviceToDevice, st), "clone") &&
+             cuda_ok(cudaMemcpyAsync(s->d_inv_perm, src->d_inv_perm, T * 4, cudaMemcpyDeviceToDevice, st), "clone");
+    if (ok && src->d_rmask)
+        ok = cuda_ok(cudaMemcpyAsync(s->d_rmask, src->d_rmask, Tpad * 4, cudaMemcpyDeviceToDevice, st), "clone");
+    if (!ok || !cuda_ok(cudaStreamSynchronize(st), "steps_sim_clone")) return STEPS_ERR_CUDA;
+    *out = s.release();
+    return STEPS_OK;
+}
+
+int steps_sim_device_bytes(const steps_sim *sim, int64_t *bytes) {
+    CHECK_NULL(sim, "steps_sim_device_bytes");
+    CHECK_NULL(bytes, "steps_sim_device_bytes");
+    const int64_t Tpad = sim->Tpad, S = sim->S, T = sim->T;
+    *bytes = 2 * S * Tpad * 4 + Tpad * 16 * 2 + Tpad * 4 + 12 + S * T * 4 + (sim->d_orig ? Tpad * 4 + T * 4 : 0) +
+             (sim->d_rmask ? Tpad * 4 : 0);
+    return STEPS_OK;
+}
+
 void steps_sim_destroy(steps_sim *sim) {
     if (!sim) return;
     if (sim->stream) cudaStreamSynchronize(sim->stream);

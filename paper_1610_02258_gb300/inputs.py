@@ -416,3 +416,77 @@ def replicate_mesh(verts: np.ndarray, tets: np.ndarray, n: int, spacing: float):
     v = (verts[None] + shift).reshape(-1, 3)
     t = (tets[None].astype(np.int64) + (np.arange(n) * nv)[:, None, None]).reshape(-1, 4)
     return v, t.astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# served job stream
+# --------------------------------------------------------------------------
+
+SIZE_BUCKETS = np.unique(np.round(np.geomspace(2_000, 1_000_000, 10)).astype(np.int64))
+
+
+def bucket_of(n_tets: int) -> int:
+    """Nearest size bucket (log scale) for a requested tet count."""
+    i = int(np.argmin(np.abs(np.log(SIZE_BUCKETS) - np.log(max(n_tets, 1)))))
+    return int(SIZE_BUCKETS[i])
+
+
+def config1_scaled(target: int, seed: int = 3, t_end: float = 10e-3):
+    """Config-1 chemistry (A + B <-> C) on a 4x4xL grid of 0.5 um cubes sized
+    to about `target` tets, 125 A and 125 B per um^3."""
+    L = max(1, int(round(target / 96)))
+    verts, tets = kuhn_box_mesh(4, 4, L, 0.5 * UM)
+    m = config1_model()
+    nt = tets.shape[0]
+    n = int(round(125.0 * 2 * 2 * L * 0.5))
+    counts = np.zeros((3, nt), np.int32)
+    counts[0] = place_uniform(n, nt, seed=2)
+    counts[1] = place_uniform(n, nt, seed=12)
+    return Workload(f"cuboid-{nt}tets-A+B<->C", verts, tets, m, counts, t_end, seed)
+
+
+def config3_scaled(target: int, seed: int = 3, t_end: float = 50e-3):
+    """Config-3 dendrite and calcium network, voxel edge chosen so that the
+    mesh has about `target` tets (0.149 um gives ~1.03M)."""
+    h = 0.149 * UM * (1.03e6 / max(target, 1)) ** (1.0 / 3.0)
+    return config3(seed=seed, h=h, t_end=t_end)
+
+
+def make_job_workload(kind: int, size: int, seed: int, t_end: float):
+    """Workload of a served job: generator `kind` (1, 2 or 3) scaled to about
+    `size` tets."""
+    if kind == 1:
+        w = config1_scaled(size, seed=seed, t_end=t_end)
+    elif kind == 2:
+        w = box_for_tets(size, seed=seed, t_end=t_end)
+    else:
+        w = config3_scaled(size, seed=seed, t_end=t_end)
+    w.t_end = t_end
+    w.seed = seed
+    return w
+
+
+@dataclass
+class JobSpec:
+    job_id: int
+    arrival: float   # seconds after the stream starts
+    kind: int        # generator 1, 2 or 3
+    size: int        # size bucket (tets, approximate)
+    seed: int
+    t_end: float     # simulated seconds
+
+
+def served_jobs(n: int, rate: float = 50.0, seed: int = 21, t_range=(1e-3, 100e-3),
+                size_range=(2_000, 1_000_000)):
+    """Poisson arrival stream (mean `rate` jobs/s) of n jobs; generator uniform
+    over configs 1-3, size log-uniform in size_range (snapped to a bucket),
+    t_end log-uniform in t_range, distinct seeds."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    t -= t[0]
+    jobs = []
+    for j in range(n):
+        size = float(np.exp(rng.uniform(np.log(size_range[0]), np.log(size_range[1]))))
+        t_end = float(np.exp(rng.uniform(np.log(t_range[0]), np.log(t_range[1]))))
+        jobs.append(JobSpec(j, float(t[j]), int(rng.integers(1, 4)), bucket_of(int(size)), 5000 + j, t_end))
+    return jobs
