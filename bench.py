@@ -106,6 +106,50 @@ class Clocks:
                 "samples": len(sm)}
 
 
+KERNEL_SOURCES = ["paper_1610_02258_gb300/csrc/steps_step.cuh", "paper_1610_02258_gb300/csrc/steps_kernels.cu",
+                  "paper_1610_02258_gb300/csrc/steps_batch.cu", "paper_1610_02258_gb300/csrc/steps_internal.h"]
+
+
+def kernel_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(name: str):
+    """DRAM bytes per launch recorded by ncu in profiles/<name>_traffic.txt,
+    or None when the file is missing or the kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", name + "_traffic.txt")
+    try:
+        kv = dict(line.split(":", 1) for line in open(path) if ":" in line)
+    except OSError:
+        return None
+    if kv.get("kernel_sources_sha256_16", "").strip() != kernel_sources_hash():
+        return None
+    return {k.strip(): int(v) for k, v in kv.items() if k.strip().endswith("bytes") or k.strip() == "bytes_per_launch"}
+
+
+def replica_seed(rank: int) -> int:
+    """Seed of the replica a rank runs (ranks run independent replicas)."""
+    return 3 + rank
+
+
+def reduce_over_ranks(ms: float, units: float):
+    """Whole-job timing over ranks: the slowest rank's time and the units of
+    all ranks (torch.distributed must be initialised)."""
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def oracle_rate(w, windows: int):
     """Serial oracle on `windows` full windows of the workload (1 core)."""
     import oracle
@@ -115,6 +159,88 @@ def oracle_rate(w, windows: int):
         o.step(o.tau)
     dt = time.perf_counter() - t0
     return w.n_tets * windows / dt, dt
+
+
+def measure_batched(args, capi, I, torch, peak):
+    """Batched form: 256 replicates of config-2-style boxes, sizes log-uniform in
+    [10k, 300k] tets, distinct seeds, 20 ms per step, one launch per window for
+    all replicates, CUDA-graph replay, autotuned block size."""
+    sizes = I.batch_sizes(n=args.batch_replicates)
+    t0 = time.perf_counter()
+    ws = [I.box_for_tets(int(sz), seed=1000 + j) for j, sz in enumerate(sizes)]
+    stream = torch.cuda.current_stream()
+    sims = [capi.from_workload(w, cuda_stream=stream.cuda_stream) for w in ws]
+    setup_s = time.perf_counter() - t0
+    batch = capi.Batch(sims, block=0, cuda_stream=stream.cuda_stream)
+    T = np.array([s.nt for s in sims], dtype=np.int64)
+    S = ws[0].model.n_species
+
+    def step():
+        batch.run([s.time + 20e-3 for s in sims])
+
+    step()  # autotune + warm
+    for _ in range(2):
+        step()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    w0 = np.array([s.windows for s in sims])
+    steps = max(2, min(args.steps, 5))
+    ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    w1 = np.array([s.windows for s in sims])
+    units = float(((w1 - w0) * T).sum())
+    launches = int(max(w1 - w0))
+    achieved = units * (8 * S + 36) / (ms / 1e3) / 1e9
+    blk, _, tune = batch.info
+    tr = profile_traffic("step_kernel_batch_config4_32rep")
+    # captured on 32 replicates (2,512,566 tets); traffic grows with the tets of a launch
+    traffic = tr["bytes_per_launch"] / 2512566 * float(T.sum()) if tr else None
+    out = {"value": units / (ms / 1e3), "unit": UNIT, "replicates": len(sims), "tets": int(T.sum()),
+           "tets_min": int(T.min()), "tets_max": int(T.max()), "ms_per_step": ms / steps, "steps": steps,
+           "windows_per_step_max": launches / steps, "block": blk, "autotune_ms_per_window": tune,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": traffic, "traffic_note": "ncu DRAM bytes per launch on 32 replicates, scaled by tets"},
+           "setup_s": setup_s, "l2": "working set > L2; also flushed before each step"}
+    batch.close()
+    for s in sims:
+        s.close()
+    return out
+
+
+def measure_served(args, capi, I):
+    """Served form: Poisson stream (50 jobs/s) of jobs from the config 1-3
+    generators, 2k-1M tets, t_end 1-100 ms, admitted by a device-memory budget,
+    continuously batched; the same jobs alone in plain form, one after another."""
+    import torch
+    from paper_1610_02258_gb300 import serve
+    jobs = I.served_jobs(args.served_jobs, rate=50.0, seed=21)
+    protos = serve.Prototypes()
+    t0 = time.perf_counter()
+    for j in jobs:
+        protos.sim(j.kind, j.size)
+    setup_s = time.perf_counter() - t0
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(free * 0.8, 64 << 30))
+    srv = serve.Server(hbm_budget=budget, max_jobs=128, wave_windows=32)
+    srv.protos = protos
+    mixed = srv.run(jobs, realtime=True)
+    s_mixed = serve.summarize(mixed, srv.stats["makespan"])
+    alone, mk = serve.run_alone(jobs, protos, realtime=True)
+    s_alone = serve.summarize(alone, mk)
+    same = all(np.array_equal(mixed[j.job_id].counts, alone[j.job_id].counts) for j in jobs)
+    protos.close()
+    return {"jobs": len(jobs), "rate_jobs_per_s": 50.0, "hbm_budget_bytes": budget,
+            "continuous": {k: s_mixed[k] for k in ("throughput", "p50_s", "p99_s", "mean_s", "makespan_s")},
+            "alone_plain": {k: s_alone[k] for k in ("throughput", "p50_s", "p99_s", "mean_s", "makespan_s")},
+            "unit": UNIT, "results_identical": bool(same), "max_active": srv.stats["max_active"],
+            "waves": srv.stats["waves"], "prototype_setup_s": setup_s}
 
 
 def run_reference(args):
@@ -158,7 +284,7 @@ def run_ours(args):
     from paper_1610_02258_gb300 import capi
     from paper_1610_02258_gb300 import inputs as I
 
-    w = I.config2(seed=3 + rank)
+    w = I.config2(seed=replica_seed(rank))
     stream = torch.cuda.current_stream()
     sim = capi.from_workload(w, cuda_stream=stream.cuda_stream)
     tau = sim.tau
@@ -190,11 +316,7 @@ def run_ours(args):
     windows = w1 - w0
     units = w.n_tets * windows
     if world > 1:
-        t = torch.tensor([ms, float(units)], device="cuda", dtype=torch.float64)
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        ms_all, units_all = float(tmax[0]), float(t[1])
+        ms_all, units_all = reduce_over_ranks(ms, float(units))
     else:
         ms_all, units_all = ms, float(units)
     value = units_all / (ms_all / 1e3)
@@ -225,13 +347,8 @@ def run_ours(args):
     kernel_s = (ms / 1e3) / windows
     achieved = w.n_tets * bytes_per_tet / kernel_s / 1e9
     peak, peak_kind = _peaks()
-    prof = os.path.join(ROOT, "profiles", "traffic_step_kernel_config2.json")
-    traffic = None
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    tr = profile_traffic("step_kernel_config2")
+    traffic = tr["bytes_per_launch"] if tr else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
@@ -248,6 +365,10 @@ def run_ours(args):
                      "bytes_per_tet_update": bytes_per_tet, "kernel_us_avg": kernel_s * 1e6},
         "clocks": clk,
     }
+    if world == 1 and not args.no_forms:
+        line["forms"] = {"plain": {"value": value, "unit": UNIT, "workload": w.name},
+                         "batched": measure_batched(args, capi, I, torch, peak) if args.batch_replicates > 0 else None,
+                         "served": measure_served(args, capi, I) if args.served_jobs > 0 else None}
     if world == 1 and not args.no_cpu_baseline:
         cpu_windows = args.cpu_windows
         rate, dt = oracle_rate(w, cpu_windows)
@@ -266,6 +387,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-windows", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--batch-replicates", type=int, default=256)
+    ap.add_argument("--served-jobs", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
