@@ -214,6 +214,54 @@ def measure_batched(args, capi, I, torch, peak):
     return out
 
 
+def measure_dendrite(args, capi, I, torch, peak):
+    """Plain form on the dendrite workload: ~1M tets, 20-species calcium
+    network with masked influx, tau = 3.3 us. One step advances the simulation
+    by --dendrite-ms of simulated time (about 300 windows per ms). Its counts
+    and tables (~210 MB) exceed L2, so this is the HBM-bound case."""
+    t0 = time.perf_counter()
+    w = I.config3()
+    stream = torch.cuda.current_stream()
+    sim = capi.from_workload(w, cuda_stream=stream.cuda_stream)
+    setup_s = time.perf_counter() - t0
+    t_step = args.dendrite_ms * 1e-3
+
+    def step():
+        sim.run(sim.time + t_step)
+
+    for _ in range(3):
+        step()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    w0, _ = capi.steps_get_windows(sim._sim)
+    steps = max(3, min(args.steps, 10))
+    ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    w1, _ = capi.steps_get_windows(sim._sim)
+    windows = w1 - w0
+    S = w.model.n_species
+    bytes_per_tet = 8 * S + 36 + (4 if w.reac_masks else 0)
+    kernel_s = (ms / 1e3) / windows
+    achieved = w.n_tets * bytes_per_tet / kernel_s / 1e9
+    tr = profile_traffic("step_kernel_dendrite")
+    out = {"value": w.n_tets * windows / (ms / 1e3), "unit": UNIT, "workload": w.name, "tets": w.n_tets,
+           "species": S, "reactions": w.model.n_reac, "tau_us": sim.tau * 1e6, "sim_ms_per_step": args.dendrite_ms,
+           "windows_per_step": windows / steps, "ms_per_step": ms / steps, "steps": steps,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": tr["bytes_per_launch"] if tr else None, "bytes_per_tet_update": bytes_per_tet,
+                        "kernel_us_avg": kernel_s * 1e6},
+           "setup_s": setup_s, "l2": "working set > L2; also flushed before each step"}
+    sim.close()
+    return out
+
+
 def measure_served(args, capi, I):
     """Served form: Poisson stream (50 jobs/s) of jobs from the config 1-3
     generators, 2k-1M tets, t_end 1-100 ms, admitted by a device-memory budget,
@@ -284,12 +332,15 @@ def run_ours(args):
     from paper_1610_02258_gb300 import capi
     from paper_1610_02258_gb300 import inputs as I
 
-    w = I.config2(seed=replica_seed(rank))
+    if args.workload == "dendrite":
+        w = I.config3(seed=replica_seed(rank))
+    else:
+        w = I.config2(seed=replica_seed(rank))
     stream = torch.cuda.current_stream()
     sim = capi.from_workload(w, cuda_stream=stream.cuda_stream)
     tau = sim.tau
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    t_step = w.t_end
+    t_step = args.sim_ms * 1e-3 if args.sim_ms > 0 else w.t_end
 
     def step():
         sim.run(sim.time + t_step)
@@ -343,11 +394,11 @@ def run_ours(args):
             torch.distributed.barrier()
         return
     S = w.model.n_species
-    bytes_per_tet = 8 * S + 36
+    bytes_per_tet = 8 * S + 36 + (4 if w.reac_masks else 0)
     kernel_s = (ms / 1e3) / windows
     achieved = w.n_tets * bytes_per_tet / kernel_s / 1e9
     peak, peak_kind = _peaks()
-    tr = profile_traffic("step_kernel_config2")
+    tr = profile_traffic("step_kernel_dendrite" if args.workload == "dendrite" else "step_kernel_config2")
     traffic = tr["bytes_per_launch"] if tr else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -365,8 +416,9 @@ def run_ours(args):
                      "bytes_per_tet_update": bytes_per_tet, "kernel_us_avg": kernel_s * 1e6},
         "clocks": clk,
     }
-    if world == 1 and not args.no_forms:
+    if world == 1 and not args.no_forms and args.workload == "irregular-box":
         line["forms"] = {"plain": {"value": value, "unit": UNIT, "workload": w.name},
+                         "plain_dendrite": measure_dendrite(args, capi, I, torch, peak) if args.dendrite_ms > 0 else None,
                          "batched": measure_batched(args, capi, I, torch, peak) if args.batch_replicates > 0 else None,
                          "served": measure_served(args, capi, I) if args.served_jobs > 0 else None}
     if world == 1 and not args.no_cpu_baseline:
@@ -390,6 +442,13 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--batch-replicates", type=int, default=256)
     ap.add_argument("--served-jobs", type=int, default=200)
+    ap.add_argument("--workload", default="irregular-box", choices=["irregular-box", "dendrite"],
+                    help="plain workload of the headline line: the 294,780-tet jittered box (default) or the "
+                         "1.03M-tet dendrite")
+    ap.add_argument("--sim-ms", type=float, default=0.0,
+                    help="simulated ms per step of the headline workload (default: its t_end)")
+    ap.add_argument("--dendrite-ms", type=float, default=1.0,
+                    help="simulated ms per step of the dendrite measurement (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

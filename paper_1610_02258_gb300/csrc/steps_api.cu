@@ -653,6 +653,7 @@ struct steps_batch {
     bool autotune = false;
     bool use_graph = true;
     int max_S = 1, max_R = 0;
+    bool any_order0 = false;
     RepEntry *h_reps = nullptr;  // pinned host mirror
     RepEntry *d_reps = nullptr;
     uint32_t *d_err = nullptr;
@@ -697,7 +698,7 @@ struct steps_batch {
 
     int window(int b, cudaStream_t st) {  // one batched window + advance
         Work &w = work[slot(b)];
-        int rc = launch_step_batch(w.d, w.n, d_reps, max_S, max_R, b, st);
+        int rc = launch_step_batch(w.d, w.n, d_reps, max_S, max_R, any_order0, b, st);
         if (!rc) rc = launch_advance(d_reps, (int32_t)members.size(), st);
         launches += 2;
         return rc;
@@ -789,6 +790,7 @@ int steps_batch_create(steps_sim *const *members, int32_t n, const steps_batch_o
         b->members.push_back(members[j]);
         b->max_S = std::max(b->max_S, members[j]->S);
         b->max_R = std::max(b->max_R, members[j]->model.R);
+        b->any_order0 = b->any_order0 || members[j]->model.dev.order0 != 0u;
     }
     if (!cuda_ok(cudaMallocHost((void **)&b->h_reps, sizeof(RepEntry) * n), "steps_batch_create: host alloc") ||
         !cuda_ok(cudaMalloc((void **)&b->d_reps, sizeof(RepEntry) * n), "steps_batch_create: alloc") ||

@@ -10,7 +10,7 @@ namespace steps {
 
 namespace {
 
-template <int BLOCK, int RM>
+template <int BLOCK, int RM, bool Z>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2)
     step_kernel_batch(const BlockWork *__restrict__ work, const RepEntry *__restrict__ reps) {
     __shared__ __align__(16) ModelDev t_model;
@@ -33,26 +33,26 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2)
         t_tile = bw.tile;
     }
     __syncthreads();
-    step_tile<BLOCK, RM>(t_model, t_args, (int64_t)t_tile);
+    step_tile<BLOCK, RM, Z>(t_model, t_args, (int64_t)t_tile);
 }
 
-template <int BLOCK, int RM>
+template <int BLOCK, int RM, bool Z>
 int launch_batch_t(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, void *stream) {
-    const size_t smem = 2 * (size_t)max_S * BLOCK * sizeof(int32_t);
+    const size_t smem = (2 * (size_t)max_S + 1) * BLOCK * sizeof(int32_t);
     static size_t static_smem = [] {
         cudaFuncAttributes fa{};
-        return cudaFuncGetAttributes(&fa, step_kernel_batch<BLOCK, RM>) == cudaSuccess ? fa.sharedSizeBytes
+        return cudaFuncGetAttributes(&fa, step_kernel_batch<BLOCK, RM, Z>) == cudaSuccess ? fa.sharedSizeBytes
                                                                                         : (size_t)0;
     }();
     if (smem + static_smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel_batch<BLOCK, RM>,
+        cudaError_t e = cudaFuncSetAttribute(step_kernel_batch<BLOCK, RM, Z>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) {
             set_error(std::string("batched step kernel shared memory: ") + cudaGetErrorString(e));
             return STEPS_ERR_CUDA;
         }
     }
-    step_kernel_batch<BLOCK, RM><<<(unsigned)nblocks, BLOCK, smem, (cudaStream_t)stream>>>(work, reps);
+    step_kernel_batch<BLOCK, RM, Z><<<(unsigned)nblocks, BLOCK, smem, (cudaStream_t)stream>>>(work, reps);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error(std::string("batched step kernel launch: ") + cudaGetErrorString(e));
@@ -61,12 +61,20 @@ int launch_batch_t(const BlockWork *work, int64_t nblocks, RepEntry *reps, int m
     return STEPS_OK;
 }
 
+template <int BLOCK, bool Z>
+int launch_batch_z(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R, void *stream) {
+    if (max_R <= 8) return launch_batch_t<BLOCK, 8, Z>(work, nblocks, reps, max_S, stream);
+    if (max_R <= 16) return launch_batch_t<BLOCK, 16, Z>(work, nblocks, reps, max_S, stream);
+    if (max_R <= 24) return launch_batch_t<BLOCK, 24, Z>(work, nblocks, reps, max_S, stream);
+    return launch_batch_t<BLOCK, 32, Z>(work, nblocks, reps, max_S, stream);
+}
+
+// Z: some member's model has order-0 reactions
 template <int BLOCK>
-int launch_batch_b(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R, void *stream) {
-    if (max_R <= 8) return launch_batch_t<BLOCK, 8>(work, nblocks, reps, max_S, stream);
-    if (max_R <= 16) return launch_batch_t<BLOCK, 16>(work, nblocks, reps, max_S, stream);
-    if (max_R <= 24) return launch_batch_t<BLOCK, 24>(work, nblocks, reps, max_S, stream);
-    return launch_batch_t<BLOCK, 32>(work, nblocks, reps, max_S, stream);
+int launch_batch_b(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R, bool any_order0,
+                   void *stream) {
+    return any_order0 ? launch_batch_z<BLOCK, true>(work, nblocks, reps, max_S, max_R, stream)
+                      : launch_batch_z<BLOCK, false>(work, nblocks, reps, max_S, max_R, stream);
 }
 
 __global__ void advance_kernel(RepEntry *reps, int32_t n) {
@@ -81,14 +89,14 @@ __global__ void advance_kernel(RepEntry *reps, int32_t n) {
 
 }  // namespace
 
-int launch_step_batch(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R, int block,
-                      void *stream) {
+int launch_step_batch(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R,
+                      bool any_order0, int block, void *stream) {
     if (nblocks <= 0) return STEPS_OK;
     switch (block) {
-    case 64: return launch_batch_b<64>(work, nblocks, reps, max_S, max_R, stream);
-    case 128: return launch_batch_b<128>(work, nblocks, reps, max_S, max_R, stream);
-    case 512: return launch_batch_b<512>(work, nblocks, reps, max_S, max_R, stream);
-    default: return launch_batch_b<256>(work, nblocks, reps, max_S, max_R, stream);
+    case 64: return launch_batch_b<64>(work, nblocks, reps, max_S, max_R, any_order0, stream);
+    case 128: return launch_batch_b<128>(work, nblocks, reps, max_S, max_R, any_order0, stream);
+    case 512: return launch_batch_b<512>(work, nblocks, reps, max_S, max_R, any_order0, stream);
+    default: return launch_batch_b<256>(work, nblocks, reps, max_S, max_R, any_order0, stream);
     }
 }
 

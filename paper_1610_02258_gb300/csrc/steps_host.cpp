@@ -216,10 +216,13 @@ int build_model(int32_t S, const double *D, int32_t R, const int32_t *lhs, const
             return STEPS_ERR_MODEL;
         }
         d.k = (float)k[r];
-        d.ra = (int8_t)ra;
-        d.rb = (int8_t)rb;
-        d.nchg = (int8_t)nchg;
+        d.need = (ra >= 0 ? 1u << ra : 0u) | (rb >= 0 ? 1u << rb : 0u);
+        d.nchg = nchg;
         d.type = order == 0 ? kOrder0 : order == 1 ? kOrder1 : (ra == rb ? kDimer : kOrder2);
+        d.ia = ra >= 0 ? ra : S;
+        d.ib = rb >= 0 ? rb : S;
+        d.sub = d.type == kDimer ? 1 : 0;
+        if (d.type == kOrder0) m.dev.order0 |= 1u << r;
     }
     return STEPS_OK;
 }

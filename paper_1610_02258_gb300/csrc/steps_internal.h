@@ -32,11 +32,17 @@ enum ReacType : int8_t { kOrder0 = 0, kOrder1 = 1, kOrder2 = 2, kDimer = 3 };
 void set_error(const std::string &msg);
 
 // ---------------------------------------------------------------- device-side model
+// Propensity a = ((c x) y) in float with x = count of species ia, y = count
+// of species ib minus sub; row S of the kernel's count tile holds 1, so a
+// missing reactant reads 1. c = k (order 1), k / (N_A V) (order 2 and dimer:
+// y = n - 1) or k N_A V (order 0), the last two computed per tet.
 struct ReacDesc {
     float k;                      // rate constant, float
-    int8_t type;                  // ReacType
-    int8_t ra, rb;                // reactant species (lower index first), -1 = none
-    int8_t nchg;                  // species changed (delta != 0), increasing species order
+    uint32_t need;                // bit s set when species s is a reactant (a_r = 0 unless all are present)
+    int32_t ia, ib;               // count rows read for x and y (S = the row of ones)
+    int32_t sub;                  // subtracted from y: 1 for a dimer, else 0
+    int32_t type;                 // ReacType
+    int32_t nchg;                 // species changed (delta != 0), increasing species order
     int8_t chg_s[kMaxChanges];
     int8_t chg_d[kMaxChanges];
 };
@@ -44,6 +50,7 @@ struct ReacDesc {
 struct ModelDev {
     int32_t S, R;
     uint32_t diffusive;           // bit s set when D_s > 0
+    uint32_t order0;              // bit r set when reaction r has order 0
     ReacDesc reac[kMaxReac];
 };
 
@@ -126,8 +133,8 @@ int launch_step(const ModelDev &m, const StepArgs &a, int block, void *stream);
 int launch_philox_test(uint64_t seed, const uint32_t *d_ctr, int64_t n, uint32_t *d_out, void *stream);
 int launch_logf_test(const float *d_x, int64_t n, float *d_out, void *stream);
 int launch_add_u64(uint64_t *p, uint64_t v, void *stream);
-int launch_step_batch(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R, int block,
-                      void *stream);
+int launch_step_batch(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R,
+                      bool any_order0, int block, void *stream);
 int launch_advance(RepEntry *reps, int32_t n, void *stream);
 
 }  // namespace steps

@@ -6,10 +6,10 @@ namespace steps {
 
 namespace {
 
-template <int BLOCK, int RM>
+template <int BLOCK, int RM, bool Z>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2)
     step_kernel(const __grid_constant__ ModelDev m, const __grid_constant__ StepArgs a) {
-    step_tile<BLOCK, RM>(m, a, (int64_t)blockIdx.x);
+    step_tile<BLOCK, RM, Z>(m, a, (int64_t)blockIdx.x);
 }
 
 __global__ void philox_test_kernel(uint32_t k0, uint32_t k1, const uint4 *ctr, int64_t n, uint4 *out) {
@@ -27,24 +27,24 @@ __global__ void logf_test_kernel(const float *x, int64_t n, float *out) {
 
 __global__ void add_u64_kernel(uint64_t *p, uint64_t v) { *p += v; }
 
-template <int BLOCK, int RM>
+template <int BLOCK, int RM, bool Z>
 int launch_step_t(const ModelDev &m, const StepArgs &a, void *stream) {
     const int64_t grid = (a.T + BLOCK - 1) / BLOCK;
-    const size_t smem = 2 * (size_t)m.S * BLOCK * sizeof(int32_t);
+    const size_t smem = (2 * (size_t)m.S + 1) * BLOCK * sizeof(int32_t);
     static size_t static_smem = [] {
         cudaFuncAttributes fa{};
-        return cudaFuncGetAttributes(&fa, step_kernel<BLOCK, RM>) == cudaSuccess ? fa.sharedSizeBytes
+        return cudaFuncGetAttributes(&fa, step_kernel<BLOCK, RM, Z>) == cudaSuccess ? fa.sharedSizeBytes
                                                                                          : (size_t)0;
     }();
     if (smem + static_smem > 48 * 1024) {  // opt in to more than the default 48 KB per block
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<BLOCK, RM>,
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<BLOCK, RM, Z>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) {
             set_error(std::string("step kernel shared memory: ") + cudaGetErrorString(e));
             return STEPS_ERR_CUDA;
         }
     }
-    step_kernel<BLOCK, RM><<<(unsigned)grid, BLOCK, smem, (cudaStream_t)stream>>>(m, a);
+    step_kernel<BLOCK, RM, Z><<<(unsigned)grid, BLOCK, smem, (cudaStream_t)stream>>>(m, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error(std::string("step kernel launch: ") + cudaGetErrorString(e));
@@ -54,12 +54,18 @@ int launch_step_t(const ModelDev &m, const StepArgs &a, void *stream) {
 }
 
 // reaction loops are unrolled to the smallest bucket of 8, 16, 24 or 32 that holds the model
+// (and to models with or without order-0 reactions)
+template <int BLOCK, bool Z>
+int launch_step_z(const ModelDev &m, const StepArgs &a, void *stream) {
+    if (m.R <= 8) return launch_step_t<BLOCK, 8, Z>(m, a, stream);
+    if (m.R <= 16) return launch_step_t<BLOCK, 16, Z>(m, a, stream);
+    if (m.R <= 24) return launch_step_t<BLOCK, 24, Z>(m, a, stream);
+    return launch_step_t<BLOCK, 32, Z>(m, a, stream);
+}
+
 template <int BLOCK>
 int launch_step_b(const ModelDev &m, const StepArgs &a, void *stream) {
-    if (m.R <= 8) return launch_step_t<BLOCK, 8>(m, a, stream);
-    if (m.R <= 16) return launch_step_t<BLOCK, 16>(m, a, stream);
-    if (m.R <= 24) return launch_step_t<BLOCK, 24>(m, a, stream);
-    return launch_step_t<BLOCK, 32>(m, a, stream);
+    return m.order0 ? launch_step_z<BLOCK, true>(m, a, stream) : launch_step_z<BLOCK, false>(m, a, stream);
 }
 
 }  // namespace

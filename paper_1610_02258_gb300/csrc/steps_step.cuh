@@ -118,23 +118,101 @@ __device__ __forceinline__ float unit24f(uint32_t w) {
     return __fmul_rn(__uint2float_rn((w >> 8) + 1u), 5.9604644775390625e-08f);
 }
 
-// Mass-action propensity in float (order 0: k N_A V; 1: k N; 2: k/(N_A V) N_a N_b;
-// dimer: k/(N_A V) N (N-1)).
-__device__ __forceinline__ float propensity(const ReacDesc &d, const int32_t *cnt, int stride, float inv_nav) {
-    switch (d.type) {
-    case kOrder0:
-        return __fdiv_rn(d.k, inv_nav);
-    case kOrder1:
-        return __fmul_rn(d.k, __int2float_rn(cnt[d.ra * stride]));
-    case kOrder2: {
-        const float c = __fmul_rn(d.k, inv_nav);
-        return __fmul_rn(__fmul_rn(c, __int2float_rn(cnt[d.ra * stride])), __int2float_rn(cnt[d.rb * stride]));
+// Reaction table of a tile in shared memory, one broadcast load per reaction
+// and field group. p[r] = (k, byte offset of row ia, byte offset of row ib,
+// flags) with flags bits 0-7 = sub, bit 8 = c takes the factor 1/(N_A V),
+// bit 9 = order 0; chg[r] = species (bytes 0-7) and deltas (bytes 8-15) of
+// the nchg[r] species reaction r changes.
+struct RxnTab {
+    float4 p[kMaxReac];
+    uint4 chg[kMaxReac];
+    int32_t nchg[kMaxReac];
+    uint32_t need[kMaxReac];
+};
+
+template <int BLOCK>
+__device__ __forceinline__ void build_rxn_tab(const ModelDev &m, RxnTab &tb) {
+    for (int r = threadIdx.x; r < m.R; r += BLOCK) {
+        const ReacDesc &d = m.reac[r];
+        const uint32_t fl = (uint32_t)d.sub | (d.type == kOrder2 || d.type == kDimer ? 0x100u : 0u) |
+                            (d.type == kOrder0 ? 0x200u : 0u);
+        tb.p[r] = make_float4(d.k, __uint_as_float((uint32_t)(d.ia * BLOCK * 4)),
+                              __uint_as_float((uint32_t)(d.ib * BLOCK * 4)), __uint_as_float(fl));
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        for (int q = 0; q < d.nchg; ++q) {
+            w[q >> 2] |= (uint32_t)(uint8_t)d.chg_s[q] << (8 * (q & 3));
+            w[2 + (q >> 2)] |= (uint32_t)(uint8_t)d.chg_d[q] << (8 * (q & 3));
+        }
+        tb.chg[r] = make_uint4(w[0], w[1], w[2], w[3]);
+        tb.nchg[r] = d.nchg;
+        tb.need[r] = d.need;
     }
-    default: {
-        const float c = __fmul_rn(d.k, inv_nav);
-        const int32_t n = cnt[d.ra * stride];
-        return __fmul_rn(__fmul_rn(c, __int2float_rn(n)), __int2float_rn(n - 1));
+}
+
+// Mass-action propensity in float, a = ((c x) y): order 0: c = k / (1/(N_A V)),
+// x = y = 1; order 1: c = k, x = N, y = 1; order 2: c = k (1/(N_A V)),
+// x = N_a, y = N_b; dimer: the same with y = N - 1. cnt points at the tet's
+// column of the count tile (row S all ones); q is the reaction's table entry.
+__device__ __forceinline__ float propensity(const float4 q, const int32_t *cnt, float inv_nav, bool has_order0) {
+    const uint32_t fl = __float_as_uint(q.w);
+    const int32_t x = *reinterpret_cast<const int32_t *>(reinterpret_cast<const char *>(cnt) + __float_as_uint(q.y));
+    const int32_t y = *reinterpret_cast<const int32_t *>(reinterpret_cast<const char *>(cnt) + __float_as_uint(q.z)) -
+                      (int32_t)(fl & 0xFFu);
+    float c = __fmul_rn(q.x, (fl & 0x100u) ? inv_nav : 1.0f);
+    if (has_order0 && (fl & 0x200u)) c = __fdiv_rn(q.x, inv_nav);
+    return __fmul_rn(__fmul_rn(c, __int2float_rn(x)), __int2float_rn(y));
+}
+
+// Running sums of the propensities in reaction order, psum[r] = a_0 + ... + a_r
+// (inactive reactions contribute 0); returns a_0 + ... + a_{R-1}.
+template <int RM>
+__device__ __forceinline__ float propensity_sums(const RxnTab &tb, int R, const int32_t *cnt, float inv_nav,
+                                                 uint32_t active, bool has_order0, float *psum) {
+    float a0 = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+        if (r < R) {
+            const float ar = ((active >> r) & 1u) ? propensity(tb.p[r], cnt, inv_nav, has_order0) : 0.0f;
+            a0 = __fadd_rn(a0, ar);
+            psum[r] = a0;
+        }
     }
+    return a0;
+}
+
+// The last reaction with a positive propensity (the pick when u2 a0 reaches
+// every running sum), or -1.
+__device__ __noinline__ int last_positive(const RxnTab &tb, int R, const int32_t *cnt, float inv_nav,
+                                          uint32_t active, bool has_order0) {
+    int last = -1;
+    for (int r = 0; r < R; ++r)
+        if (((active >> r) & 1u) && propensity(tb.p[r], cnt, inv_nav, has_order0) > 0.0f) last = r;
+    return last;
+}
+
+// The reaction an event fires: the first r whose running sum exceeds
+// target = u2 a0 (running sums only grow, so that is the number of sums
+// <= target); if none does, the last reaction with a positive propensity.
+template <int RM>
+__device__ __forceinline__ int pick_reaction(const RxnTab &tb, int R, const float *psum, float target,
+                                             const int32_t *cnt, float inv_nav, uint32_t active, bool has_order0) {
+    int n = 0;
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+        if (r < R) n += psum[r] <= target ? 1 : 0;
+    return n < R ? n : last_positive(tb, R, cnt, inv_nav, active, has_order0);
+}
+
+// Applies reaction r's changes to the tet's counts (column cnt, rows BLOCK apart).
+template <int BLOCK>
+__device__ __forceinline__ void apply_changes(const RxnTab &tb, int r, int32_t *cnt) {
+    const uint4 c = tb.chg[r];
+    const int n = tb.nchg[r];
+    for (int q = 0; q < n; ++q) {
+        const uint32_t sw = q < 4 ? c.x : c.y, dw = q < 4 ? c.z : c.w;
+        const int s = (int)((sw >> (8 * (q & 3))) & 0xFFu);
+        const int d = (int)(int8_t)((dw >> (8 * (q & 3))) & 0xFFu);
+        cnt[s * BLOCK] += d;
     }
 }
 
@@ -169,246 +247,181 @@ __device__ __forceinline__ long long round_trials(double nbar, uint32_t w) {
 // Reaction SSA operator for one tet over tau_k (Algorithm 1, reaction part):
 // Gillespie's direct method with float propensities and double time, and
 // the time-weighted occupancy of every species a fired reaction changes.
-// Counts live in shared memory (cnt[s * BLOCK]); on return trial[s * BLOCK]
-// holds the integer trial count of every diffusive species the reactions
-// changed (mean occupancy, stochastically rounded, clamped to the end count;
-// or the end count in END mode). Returns error bits.
-template <int BLOCK, int RM>
-__device__ uint32_t ssa_tet(const ModelDev &m, const StepArgs &a, int32_t *cnt, int32_t *trial, uint32_t tet,
-                            uint32_t c0, uint32_t c3, float inv_nav, uint32_t active) {
-    uint32_t touched = 0, bad = 0;
-    double O[kMaxSpecies], tS[kMaxSpecies];
-    double dt_acc = 0.0;
-    uint32_t j = 0;
+// Counts live in shared memory (cnt[s * BLOCK]). The caller has already
+// fired the tet's first event (reaction pick0 at time dt0, counts updated);
+// this continues from event 1. On return `touched` has a bit for every
+// species a fired reaction changed, with its occupancy integral up to its
+// last change in O[s] and the time of that change in tS[s]. Returns error
+// bits.
+template <int BLOCK, int RM, bool Z>
+__device__ uint32_t ssa_tet(const RxnTab &tb, const ModelDev &m, const StepArgs &a, int32_t *cnt, uint32_t tet,
+                            uint32_t c0, uint32_t c3, float inv_nav, uint32_t active, int pick0, float dt0, double *O,
+                            double *tS, uint32_t &touched) {
+    uint32_t bad = 0;
+    touched = 0;
+    constexpr bool has0 = Z;
+    double dt_acc = (double)dt0;  // 0 + (double)dt0: exact
+    {
+        // occupancy after the first event: O_S = n_before * dt0 (0 + n (dt - 0), both steps exact)
+        const uint4 c = tb.chg[pick0];
+        const int n = tb.nchg[pick0];
+        for (int q = 0; q < n; ++q) {
+            const uint32_t sw = q < 4 ? c.x : c.y, dw = q < 4 ? c.z : c.w;
+            const int s = (int)((sw >> (8 * (q & 3))) & 0xFFu);
+            const int d = (int)(int8_t)((dw >> (8 * (q & 3))) & 0xFFu);
+            O[s] = __dmul_rn((double)(cnt[s * BLOCK] - d), dt_acc);
+            tS[s] = dt_acc;
+            touched |= 1u << s;
+        }
+    }
+    uint32_t j = 1;
     for (;;) {
-        // keep the model's constants out of registers across iterations (the
-        // batched kernel reads them from shared memory)
+        // keep the reaction table out of registers across iterations
         asm volatile("" ::: "memory");
         // the attempt's two uniforms do not depend on the state: start them first
         const uint4 w = philox4x32_10(a.key0, a.key1, c0, tet, j, (kPurposeReac << 28) | c3);
         const float neg_log_u1 = -steps_logf(unit24f(w.x));
         const float u2 = unit24f(w.y);
-        // propensities; psum[r] = a_0 + ... + a_r summed in reaction order
         float psum[RM];
-        uint32_t pos = 0;
-        float a0 = 0.0f;
-#pragma unroll
-        for (int r = 0; r < RM; ++r) {
-            if (r < m.R) {
-                const float ar = ((active >> r) & 1u) ? propensity(m.reac[r], cnt, BLOCK, inv_nav) : 0.0f;
-                a0 = __fadd_rn(a0, ar);
-                psum[r] = a0;
-                pos |= (ar > 0.0f ? 1u : 0u) << r;
-            }
-        }
+        const float a0 = propensity_sums<RM>(tb, m.R, cnt, inv_nav, active, has0, psum);
         if (!(a0 > 0.0f)) break;
         if (j >= kMaxEventsPerWindow) {  // pathological rates: stop and report, never spin
             bad |= 2u;
             break;
         }
         const float dt = __fdiv_rn(neg_log_u1, a0);
-        double dt_new;
-        if (j == 0) {
-            // 0 + (double)dt is exact, and (double)dt > tau_k <=> dt > tau_dn
-            if (dt > a.tau_dn) break;
-            dt_new = (double)dt;
-        } else {
-            dt_new = __dadd_rn(dt_acc, (double)dt);
-            if (dt_new > a.tau_k) break;
-        }
+        const double dt_new = __dadd_rn(dt_acc, (double)dt);
+        if (dt_new > a.tau_k) break;
         ++j;
-        // first reaction whose running sum exceeds u2 a0 (running sums only grow,
-        // so the reactions past the target form a suffix); if none, the last
-        // reaction with a positive propensity
-        const float target = __fmul_rn(u2, a0);
-        uint32_t over = 0;
-#pragma unroll
-        for (int r = 0; r < RM; ++r)
-            if (r < m.R) over |= (psum[r] > target ? 1u : 0u) << r;
-        const int pick = over ? __ffs(over) - 1 : (pos ? 31 - __clz(pos) : -1);
+        const int pick = pick_reaction<RM>(tb, m.R, psum, __fmul_rn(u2, a0), cnt, inv_nav, active, has0);
         if (pick < 0) break;
         dt_acc = dt_new;
-        const ReacDesc &d = m.reac[pick];
-        for (int q = 0; q < d.nchg; ++q) {
-            const int s = d.chg_s[q];
-            const int32_t n = cnt[s * BLOCK];
+        const uint4 c = tb.chg[pick];
+        const int n = tb.nchg[pick];
+        for (int q = 0; q < n; ++q) {
+            const uint32_t sw = q < 4 ? c.x : c.y, dw = q < 4 ? c.z : c.w;
+            const int s = (int)((sw >> (8 * (q & 3))) & 0xFFu);
+            const int d = (int)(int8_t)((dw >> (8 * (q & 3))) & 0xFFu);
+            const int32_t nn = cnt[s * BLOCK];
             if ((touched >> s) & 1u) {
-                O[s] = __dadd_rn(O[s], __dmul_rn((double)n, __dsub_rn(dt_acc, tS[s])));
+                O[s] = __dadd_rn(O[s], __dmul_rn((double)nn, __dsub_rn(dt_acc, tS[s])));
             } else {
-                O[s] = __dmul_rn((double)n, dt_acc);  // 0 + n (dt - 0): both steps exact
+                O[s] = __dmul_rn((double)nn, dt_acc);  // 0 + n (dt - 0): both steps exact
             }
             tS[s] = dt_acc;
             touched |= 1u << s;
-            cnt[s * BLOCK] = n + d.chg_d[q];
+            cnt[s * BLOCK] = nn + d;
         }
-    }
-    // trial counts of the changed diffusive species, one set bit at a time
-    uint32_t todo = touched & m.diffusive;
-    uint32_t rblk = 0xFFFFFFFFu;
-    uint4 rb = make_uint4(0, 0, 0, 0);
-    while (todo) {
-        const int s = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int32_t N = cnt[s * BLOCK];
-        int32_t M = N;
-        if (a.occ) {
-            // Nbar = (O_S + N_S (tau - t_S)) / tau, stochastically rounded, clamped to N_S
-            const double occ = __dadd_rn(O[s], __dmul_rn((double)N, __dsub_rn(a.tau_k, tS[s])));
-            const double nbar = __dmul_rn(occ, a.inv_tau_k);
-            if ((uint32_t)(s >> 2) != rblk) {
-                rblk = (uint32_t)(s >> 2);
-                rb = philox4x32_10(a.key0, a.key1, c0, tet, rblk, (kPurposeRound << 28) | c3);
-            }
-            const long long mm = round_trials(nbar, word_of(rb, s & 3));
-            M = mm > N ? N : (int32_t)mm;
-        }
-        trial[s * BLOCK] = M;
     }
     return bad;
 }
 
-// Trial words per phase-C work item (two Philox blocks).
-constexpr uint32_t kItemWords = 8;
-
-// Block-wide exclusive scan of one value per thread; returns the total.
-template <int BLOCK>
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *out, uint32_t *warp_tot) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-        if (lane >= d) x += y;
+// Trial count of species s of a tet with end count N (Algorithm 1, diffusion
+// operator): N if no reaction changed s (its occupancy is N over the whole
+// window) or in END mode; else the mean occupancy
+// Nbar = (O_S + N_S (tau - t_S)) / tau, stochastically rounded with word
+// s mod 4 of the tet's ROUND block s / 4, clamped to N.
+__device__ __forceinline__ int32_t trial_count(const StepArgs &a, int s, int32_t N, bool changed, const double *O,
+                                               const double *tS, uint32_t key_tet, uint32_t c0, uint32_t c3,
+                                               uint32_t &rblk, uint4 &rb) {
+    if (!changed || !a.occ) return N;
+    const double occ = __dadd_rn(O[s], __dmul_rn((double)N, __dsub_rn(a.tau_k, tS[s])));
+    const double nbar = __dmul_rn(occ, a.inv_tau_k);
+    if ((uint32_t)(s >> 2) != rblk) {
+        rblk = (uint32_t)(s >> 2);
+        rb = philox4x32_10(a.key0, a.key1, c0, key_tet, rblk, (kPurposeRound << 28) | c3);
     }
-    if (lane == 31) warp_tot[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t t = lane < BLOCK / 32 ? warp_tot[lane] : 0u;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, d);
-            if (lane >= d) t += y;
-        }
-        if (lane < BLOCK / 32) warp_tot[lane] = t;  // inclusive
-    }
-    __syncthreads();
-    const uint32_t before = wid > 0 ? warp_tot[wid - 1] : 0u;
-    out[threadIdx.x] = before + x - v;
-    const uint32_t total = warp_tot[BLOCK / 32 - 1];
-    return total;
+    const long long mm = round_trials(nbar, word_of(rb, s & 3));
+    return mm > N ? N : (int32_t)mm;
 }
 
-// Trial molecules of one tet that draw words: every diffusive species with a
-// non-zero leave threshold keeps its trial count, the others get 0 (written
-// back to trial[s * stride]). Returns their sum, the tet's word count.
-__device__ __forceinline__ uint32_t trial_words(const ModelDev &m, const StepArgs &a, const uint4 A, int32_t *trial,
-                                                int stride) {
-    uint32_t W = 0;
-    for (int s = 0; s < m.S; ++s) {
-        int32_t M = 0;
-        if ((m.diffusive >> s) & 1u) {
-            M = trial[s * stride];
-            if ((uint32_t)(((uint64_t)A.w * a.scale[s]) >> 31) == 0u) M = 0;
-        }
-        trial[s * stride] = M;
-        W += (uint32_t)M;
-    }
-    return W;
+// Leave thresholds of one species: T_f = (A_f R_s) >> 31 (2^31 fixed point).
+__device__ __forceinline__ void species_thresholds(const uint4 &A, uint32_t R, uint32_t &T0, uint32_t &T1,
+                                                   uint32_t &T2, uint32_t &T3) {
+    T0 = (uint32_t)(((uint64_t)A.x * R) >> 31);
+    T1 = (uint32_t)(((uint64_t)A.y * R) >> 31);
+    T2 = (uint32_t)(((uint64_t)A.z * R) >> 31);
+    T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
 }
 
-// Work items per block the item map holds (beyond it, items find their tet
-// and species by search).
-template <int BLOCK>
-struct ItemMap {
-    static constexpr uint32_t kCap = 4 * BLOCK;
+// Per-warp work state of the diffusion operator. The warp's chunk holds up
+// to 32 tets; their trial molecules form one stream per tet (species in
+// order), cut into Philox blocks of 4 words. Block b of the chunk belongs to
+// lane `owner` with first[lane] <= b < first[lane + 1]; the map caches the
+// owner, the species of the block's first word and the tet's trial
+// molecules before that species for the first kMapCap blocks.
+constexpr int kMapCap = 160;
+
+struct WarpWork {
+    int16_t tet[32];          // tile index of each lane's tet (-1: none)
+    uint32_t hm[32];          // species with trial molecules
+    uint32_t W[32];           // trial molecules (words) of the tet
+    uint32_t touched[32];     // species its reactions changed
+    uint32_t first[33];       // exclusive prefix of the lanes' block counts
+    uint32_t map_own[kMapCap];  // lane | species << 5 | block-in-tet << 10
+    uint32_t map_before[kMapCap];
 };
 
-// Fill the item map for this thread's tet t: item blk_start[t] + k covers
-// words [k kItemWords, (k+1) kItemWords) of the tet's stream; record the tet,
-// the species of the item's first word and the number of the tet's trial
-// molecules before that species.
+// One Philox block (4 words) of a tet's diffusion stream: word w decides
+// trial molecule w (species in order): face f when T_{f-1} <= x < T_f with
+// x = w >> 1 and cumulative thresholds T, stay when x >= T_3. A mover is
+// added to the neighbour's entry of nxt and removed from the tet's count.
 template <int BLOCK>
-__device__ __forceinline__ void map_items(int t, uint32_t W, uint32_t first, uint32_t total, const int32_t *trial,
-                                          uint32_t *owner, uint32_t *before) {
-    if (W == 0 || total > ItemMap<BLOCK>::kCap) return;
-    const uint32_t n = (W + kItemWords - 1u) / kItemWords;
-    int s = 0;
-    uint32_t pre = 0, end = (uint32_t)trial[0];
-    for (uint32_t k = 0; k < n; ++k) {
-        const uint32_t w = k * kItemWords;
-        while (w >= end) {
-            pre = end;
-            ++s;
-            end += (uint32_t)trial[s * BLOCK];
-        }
-        owner[first + k] = (uint32_t)t | ((uint32_t)s << 9) | (k << 14);
-        before[first + k] = pre;
-    }
-}
-
-// One work item of the diffusion operator: up to kItemWords consecutive words
-// of one tet's stream (two Philox blocks), each deciding one trial molecule:
-// face f when T_{f-1} <= x < T_f (cumulative thresholds), stay when x >= T_3.
-// A mover is added to the neighbour's entry of nxt and removed from this tet's
-// shared count.
-template <int BLOCK>
-__device__ __forceinline__ void diffuse_item(const StepArgs &a, uint32_t item, uint32_t total, int nlive,
-                                             const uint32_t *blk_start, const uint32_t *owner,
-                                             const uint32_t *before, const uint32_t *words,
-                                             const int32_t *trial_all, int32_t *cnt_all, const uint4 *s_thr,
-                                             const int4 *s_nbr, const uint32_t *s_tet, uint32_t c0, uint32_t c3) {
-    int t, s;
-    uint32_t w, end;
-    if (total <= ItemMap<BLOCK>::kCap) {
-        const uint32_t o = owner[item];
-        t = (int)(o & 0x1FFu);
-        s = (int)((o >> 9) & 0x1Fu);
-        w = (o >> 14) * kItemWords;
-        end = before[item] + (uint32_t)trial_all[s * BLOCK + t];
+__device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork &ww, uint32_t item,
+                                              const int32_t *trial_all, int32_t *cnt_all, const uint4 *s_thr,
+                                              const int4 *s_nbr, const uint32_t *s_tet, uint32_t c0, uint32_t c3) {
+    int lane, s;
+    uint32_t k, before;
+    if (item < (uint32_t)kMapCap) {
+        const uint32_t o = ww.map_own[item];
+        lane = (int)(o & 31u);
+        s = (int)((o >> 5) & 31u);
+        k = o >> 10;
+        before = ww.map_before[item];
     } else {
-        // the tet owning this item: last t with blk_start[t] <= item
-        int lo = 0, hi = nlive - 1;
+        // the owner: last lane with first[lane] <= item; the species: walk the tet's
+        // species until the block's first word
+        int lo = 0, hi = 31;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (blk_start[mid] <= item) lo = mid;
+            if (ww.first[mid] <= item) lo = mid;
             else hi = mid - 1;
         }
-        t = lo;
-        w = (item - blk_start[t]) * kItemWords;
-        s = 0;
-        end = (uint32_t)trial_all[t];
-        while (w >= end) {
-            ++s;
+        lane = lo;
+        k = item - ww.first[lane];
+        const int t = ww.tet[lane];
+        uint32_t hm = ww.hm[lane];
+        s = __ffs(hm) - 1;
+        before = 0;
+        uint32_t end = (uint32_t)trial_all[s * BLOCK + t];
+        while (4u * k >= end) {
+            hm &= hm - 1;
+            s = __ffs(hm) - 1;
+            before = end;
             end += (uint32_t)trial_all[s * BLOCK + t];
         }
     }
-    const int32_t *trial = trial_all + t;
-    const uint32_t Wt = words[t];
-    const uint32_t tet = s_tet[t];
+    const int t = ww.tet[lane];
+    const uint32_t Wt = ww.W[lane];
+    uint32_t hm = ww.hm[lane] & ~((2u << s) - 1u);  // species after s
+    uint32_t end = before + (uint32_t)trial_all[s * BLOCK + t];
     const uint4 A = s_thr[t];
     const int4 nb = s_nbr[t];
     const size_t Tpad = (size_t)a.Tpad;
-    // both Philox blocks of the item as independent chains (the second may go unused)
-    const uint4 rw0 = philox4x32_10(a.key0, a.key1, c0, tet, w >> 2, (kPurposeDiff << 28) | c3);
-    const uint4 rw1 = philox4x32_10(a.key0, a.key1, c0, tet, (w >> 2) + 1u, (kPurposeDiff << 28) | c3);
-    uint64_t R = a.scale[s];
-    uint32_t T0 = (uint32_t)(((uint64_t)A.x * R) >> 31), T1 = (uint32_t)(((uint64_t)A.y * R) >> 31);
-    uint32_t T2 = (uint32_t)(((uint64_t)A.z * R) >> 31), T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
+    const uint4 rw = philox4x32_10(a.key0, a.key1, c0, s_tet[t], k, (kPurposeDiff << 28) | c3);
+    uint32_t T0, T1, T2, T3;
+    species_thresholds(A, a.scale[s], T0, T1, T2, T3);
+    uint32_t w = 4u * k;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int q = 0; q < 4; ++q) {
         if (w < Wt) {
             if (w >= end) {  // next species with trial molecules
-                do {
-                    ++s;
-                    end += (uint32_t)trial[s * BLOCK];
-                } while (w >= end);
-                R = a.scale[s];
-                T0 = (uint32_t)(((uint64_t)A.x * R) >> 31);
-                T1 = (uint32_t)(((uint64_t)A.y * R) >> 31);
-                T2 = (uint32_t)(((uint64_t)A.z * R) >> 31);
-                T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
+                s = __ffs(hm) - 1;
+                hm &= hm - 1;
+                end += (uint32_t)trial_all[s * BLOCK + t];
+                species_thresholds(A, a.scale[s], T0, T1, T2, T3);
             }
-            const uint32_t x = word_of(k < 4 ? rw0 : rw1, k & 3) >> 1;
+            const uint32_t x = word_of(rw, q) >> 1;
             if (x < T3) {
                 const int nbr = x < T0 ? nb.x : x < T1 ? nb.y : x < T2 ? nb.z : nb.w;
                 atomicAdd(a.nxt + s * Tpad + nbr, 1);
@@ -419,43 +432,73 @@ __device__ __forceinline__ void diffuse_item(const StepArgs &a, uint32_t item, u
     }
 }
 
+// What stays in tet t after diffusion is added to its own entry of nxt
+// (immobile species are written by this tet alone). `may` holds the species
+// that can be non-zero (non-zero at the start or changed by a reaction).
+template <int BLOCK>
+__device__ __forceinline__ void apply_remaining(const ModelDev &m, const StepArgs &a, const int32_t *cnt_all, int t,
+                                                uint32_t may, int64_t i0) {
+    const int S = m.S;
+    uint32_t out_set = (may & m.diffusive) | (~m.diffusive & ((S < 32 ? (1u << S) : 0u) - 1u));
+    int32_t *out = a.nxt + i0 + t;
+    const size_t Tpad = (size_t)a.Tpad;
+    while (out_set) {
+        const int s = __ffs(out_set) - 1;
+        out_set &= out_set - 1;
+        const int32_t N = cnt_all[s * BLOCK + t];
+        if ((m.diffusive >> s) & 1u) {
+            if (N) atomicAdd(out + s * Tpad, N);
+        } else {
+            out[s * Tpad] = N;
+        }
+    }
+}
+
 // One diffusion window for BLOCK consecutive tets (device order).
-//  load   counts into shared memory; mobile entries of `cur` are zeroed as read
-//  A      each thread: its tet's propensities and first waiting time, in float;
-//         (double)dt > tau_k is tested as dt > tau_dn, tau_dn the largest float
-//         <= tau_k (the same decision); tets with an event are queued
-//  B      the queued tets' full SSA and trial counts, one queued tet per thread
-//  C      trial words of all the block's tets: Philox blocks of four words are
-//         spread evenly over the threads; each word moves or keeps one trial
-//         molecule; movers are added to the neighbour in `nxt` at once
-//  D      what stays is added to the tet's own entry of `nxt` (coalesced)
-template <int BLOCK, int RM>
+//  load   counts and tables into shared memory by bulk copies; each thread
+//         notes its tet's non-zero species and zeroes their mobile entries
+//         in `cur` (which receives the window after next)
+//  A      each thread: its tet's propensities (reactions no tet of the warp
+//         can fire are skipped warp-wide: their propensity is 0) and first
+//         waiting time, in float; (double)dt > tau_k is tested as
+//         dt > tau_dn, tau_dn the largest float <= tau_k (the same decision);
+//         a tet whose first event falls inside the window fires it here and
+//         is listed as reacting, the others as calm
+//  chunks each warp takes chunks of 32 listed tets (reacting tets first):
+//         the reacting tets' SSA from their second event on; trial counts;
+//         the chunk's Philox blocks of trial words (each word moves or keeps
+//         one trial molecule; movers are added to the neighbour's entry of
+//         `nxt` at once), spread over the warp's lanes for calm chunks and
+//         over the whole block, after a barrier, for chunks with reacting
+//         tets; then each tet's remaining counts are added to its own entry
+//         of `nxt`. Z: the model has order-0 reactions.
+template <int BLOCK, int RM, bool Z>
 __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, const int64_t tile) {
-    extern __shared__ __align__(16) int32_t smem[];  // cnt [S][BLOCK], trial [S][BLOCK]
+    extern __shared__ __align__(16) int32_t smem[];  // cnt [S + 1][BLOCK], trial [S][BLOCK]
     __shared__ __align__(16) uint4 s_thr[BLOCK];
     __shared__ __align__(16) int4 s_nbr[BLOCK];
     __shared__ __align__(16) uint32_t s_tet[BLOCK];
     __shared__ __align__(16) float s_inv_nav[BLOCK];
     __shared__ __align__(16) uint32_t s_mask[BLOCK];
-    __shared__ int32_t queue[BLOCK];
-    __shared__ uint32_t blk_start[BLOCK + 1];
-    __shared__ uint32_t words[BLOCK];
-    __shared__ uint32_t warp_tot[BLOCK / 32];
-    __shared__ int32_t nqueue;
-    __shared__ uint8_t reacted[BLOCK];  // 1 = queued for the full SSA
-    __shared__ uint32_t next_item;
-    __shared__ uint32_t item_owner[ItemMap<BLOCK>::kCap];
-    __shared__ uint32_t item_before[ItemMap<BLOCK>::kCap];
+    __shared__ uint32_t s_nz[BLOCK];      // species with a non-zero count at window start
+    __shared__ int16_t list[BLOCK];       // reacting tets from the front, calm tets from the back
+    __shared__ float q_dt[BLOCK];         // time of a reacting tet's first event
+    __shared__ int8_t q_pick[BLOCK];      // its reaction
+    __shared__ int32_t nreact, ncalm;
+    __shared__ uint32_t next_chunk;
+    __shared__ WarpWork wwork[BLOCK / 32];
+    __shared__ RxnTab tb;
     __shared__ __align__(8) uint64_t bar;
 
     const int S = m.S;
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int64_t i0 = tile * BLOCK;
     const int64_t i = i0 + tid;
     const int nlive = (int)min((int64_t)BLOCK, (int64_t)a.T - i0);
     const bool live = tid < nlive;
-    int32_t *cnt_all = smem;
-    int32_t *trial_all = smem + (size_t)S * BLOCK;
+    int32_t *cnt_all = smem;                              // rows 0..S-1 counts, row S ones
+    int32_t *trial_all = smem + (size_t)(S + 1) * BLOCK;
     const uint64_t window = a.window + (a.window_base ? *a.window_base : 0ull);
     const uint32_t c0 = (uint32_t)window;
     const uint32_t c3 = (uint32_t)(window >> 32) & 0x0FFFFFFFu;
@@ -465,9 +508,12 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     // ---- load: the block's tile of every table, by TMA bulk copies into
     // shared memory (rows padded to 16 bytes; the tables are padded to Tpad)
     if (tid == 0) {
-        nqueue = 0;
+        nreact = 0;
+        ncalm = 0;
+        next_chunk = 0;
         mbar_init(&bar, 1);
     }
+    build_rxn_tab<BLOCK>(m, tb);
     __syncthreads();
     if (tid == 0) {
         const uint32_t n4 = ((uint32_t)nlive + 3u) & ~3u;
@@ -483,7 +529,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     }
     if (!a.orig) s_tet[tid] = (uint32_t)i;
     if (!a.rmask) s_mask[tid] = 0xFFFFFFFFu;
-    reacted[tid] = 0;
+    cnt_all[S * BLOCK + tid] = 1;
     const bool arrived = mbar_wait_bounded(&bar, 0);
     if (__syncthreads_or(!arrived)) {
         // the copies did not land in time: report, let them finish (bounded), skip the window
@@ -494,95 +540,162 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         __syncthreads();
         return;
     }
+    uint32_t nz = 0;
     if (live) {
         for (int s = 0; s < S; ++s) {
             const int32_t v = cnt_all[s * BLOCK + tid];
             bad |= v < 0 ? 1u : 0u;
-            trial_all[s * BLOCK + tid] = v;
-            if ((m.diffusive >> s) & 1u) a.cur[s * Tpad + i] = 0;  // receives the window after next
+            nz |= (v != 0 ? 1u : 0u) << s;
+            // a mobile entry receives the window after next: zero it (it is zero already when v == 0)
+            if (v != 0 && ((m.diffusive >> s) & 1u)) a.cur[s * Tpad + i] = 0;
         }
     }
-    __syncthreads();
+    s_nz[tid] = nz;
 
-    // ---- A: does the tet's first reaction fall inside the window?
-    if (live && m.R > 0) {
+    // ---- A: the tet's first reaction event, if it falls inside the window
+    bool reacting = false;
+    if (m.R > 0) {
         const float inv_nav = s_inv_nav[tid];
-        const uint32_t active = s_mask[tid];
-        const int32_t *cnt = cnt_all + tid;
-        const uint4 w = philox4x32_10(a.key0, a.key1, c0, s_tet[tid], 0u, (kPurposeReac << 28) | c3);
-        const float neg_log_u1 = -steps_logf(unit24f(w.x));
+        const uint32_t active = live ? s_mask[tid] : 0u;
+        constexpr bool has0 = Z;
+        int32_t *cnt = cnt_all + tid;
+        float psum[RM];
         float a0 = 0.0f;
+        // a_r = 0 (exactly: a product with a zero count) unless every reactant
+        // is present; reactions no tet of the warp can fire are skipped
+        const uint32_t wnz = __reduce_or_sync(0xFFFFFFFFu, nz);
+        const uint32_t wact = __reduce_or_sync(0xFFFFFFFFu, active);
 #pragma unroll
         for (int r = 0; r < RM; ++r) {
             if (r < m.R) {
-                const float ar = ((active >> r) & 1u) ? propensity(m.reac[r], cnt, BLOCK, inv_nav) : 0.0f;
+                const uint32_t need = tb.need[r];
+                float ar = 0.0f;
+                if (((wact >> r) & 1u) && (wnz & need) == need)
+                    ar = ((active >> r) & 1u) ? propensity(tb.p[r], cnt, inv_nav, has0) : 0.0f;
                 a0 = __fadd_rn(a0, ar);
+                psum[r] = a0;
             }
         }
-        if (a0 > 0.0f) {
-            const float dt = __fdiv_rn(neg_log_u1, a0);
+        if (live && a0 > 0.0f) {
+            const uint4 w = philox4x32_10(a.key0, a.key1, c0, s_tet[tid], 0u, (kPurposeReac << 28) | c3);
+            const float dt = __fdiv_rn(-steps_logf(unit24f(w.x)), a0);
+            // 0 + (double)dt is exact, and (double)dt > tau_k <=> dt > tau_dn
             if (!(dt > a.tau_dn)) {
-                queue[atomicAdd(&nqueue, 1)] = tid;
-                reacted[tid] = 1;
+                const int pick = pick_reaction<RM>(tb, m.R, psum, __fmul_rn(unit24f(w.y), a0), cnt, inv_nav,
+                                                   active, has0);
+                if (pick >= 0) {
+                    apply_changes<BLOCK>(tb, pick, cnt);
+                    q_pick[tid] = (int8_t)pick;
+                    q_dt[tid] = dt;
+                    reacting = true;
+                }
             }
         }
     }
-    __syncthreads();
-
-    // ---- C1 + B: the tets that did not react already have their trial counts
-    // (their counts); their work items are grabbed by every warp while the
-    // first warps run the full SSA of the tets that did (B), then join in.
-    uint32_t W = (live && !reacted[tid]) ? trial_words(m, a, s_thr[tid], trial_all + tid, BLOCK) : 0u;
-    words[tid] = W;
-    uint32_t total = block_exclusive_scan<BLOCK>((W + kItemWords - 1u) / kItemWords, blk_start, warp_tot);
-    if (tid == 0) {
-        blk_start[BLOCK] = total;
-        next_item = 0;
-    }
-    map_items<BLOCK>(tid, W, blk_start[tid], total, trial_all + tid, item_owner, item_before);
-    __syncthreads();
-    const int nq = nqueue;
-    if (tid < nq) {
-        const int t = queue[tid];
-        bad |= ssa_tet<BLOCK, RM>(m, a, cnt_all + t, trial_all + t, s_tet[t], c0, c3, s_inv_nav[t], s_mask[t]);
-    }
-    __syncwarp();
-    {
-        const int lane = tid & 31;
-        for (;;) {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&next_item, 32u);
-            base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            if (base >= total) break;
-            const uint32_t item = base + (uint32_t)lane;
-            if (item < total)
-                diffuse_item<BLOCK>(a, item, total, nlive, blk_start, item_owner, item_before, words, trial_all,
-                                    cnt_all, s_thr, s_nbr, s_tet, c0, c3);
-        }
-    }
-    __syncthreads();
-    // ---- C2: the work items of the tets that reacted, now that their trial counts are known
-    W = (live && reacted[tid]) ? trial_words(m, a, s_thr[tid], trial_all + tid, BLOCK) : 0u;
-    words[tid] = W;
-    total = block_exclusive_scan<BLOCK>((W + kItemWords - 1u) / kItemWords, blk_start, warp_tot);
-    if (tid == 0) blk_start[BLOCK] = total;
-    map_items<BLOCK>(tid, W, blk_start[tid], total, trial_all + tid, item_owner, item_before);
-    __syncthreads();
-    for (uint32_t item = tid; item < total; item += BLOCK)
-        diffuse_item<BLOCK>(a, item, total, nlive, blk_start, item_owner, item_before, words, trial_all, cnt_all,
-                            s_thr, s_nbr, s_tet, c0, c3);
-    __syncthreads();
-
-    // ---- D: the molecules that stay (immobile species: written by this tet alone)
     if (live) {
-        for (int s = 0; s < S; ++s) {
-            const int32_t N = cnt_all[s * BLOCK + tid];
-            int32_t *out = a.nxt + s * Tpad + i;
-            if ((m.diffusive >> s) & 1u) {
-                if (N) atomicAdd(out, N);
-            } else {
-                *out = N;
+        if (reacting) list[atomicAdd(&nreact, 1)] = (int16_t)tid;
+        else list[BLOCK - 1 - atomicAdd(&ncalm, 1)] = (int16_t)tid;
+    }
+    __syncthreads();
+
+    // ---- phase 1: chunks of 32 listed tets (reacting tets first, then calm
+    // ones), one warp each. The reacting chunks run their SSA and trial counts
+    // and leave their diffusion to phase 2; calm chunks finish here.
+    const int nr = nreact, nc = ncalm;
+    const int rchunks = (nr + 31) >> 5;
+    const int nchunks = (nr + nc + 31) >> 5;
+    for (;;) {
+        uint32_t ch = 0;
+        if (lane == 0) ch = atomicAdd(&next_chunk, 1u);
+        ch = __shfl_sync(0xFFFFFFFFu, ch, 0);
+        if (ch >= (uint32_t)nchunks) break;
+        WarpWork &ww = wwork[ch];
+        const int j = (int)ch * 32 + lane;  // position in [reacting..., calm...]
+        const bool valid = j < nr + nc;
+        const bool reacts = j < nr;
+        const int t = !valid ? -1 : reacts ? list[j] : list[BLOCK - 1 - (j - nr)];
+
+        // the reacting tets' SSA from their second event on
+        uint32_t touched = 0;
+        double O[kMaxSpecies], tS[kMaxSpecies];
+        if (reacts)
+            bad |= ssa_tet<BLOCK, RM, Z>(tb, m, a, cnt_all + t, s_tet[t], c0, c3, s_inv_nav[t], s_mask[t],
+                                         q_pick[t], q_dt[t], O, tS, touched);
+
+        // trial counts: species that may hold molecules (non-zero at the start, or
+        // changed by a reaction), diffusive, with a non-zero leave threshold
+        uint32_t W = 0, hm = 0;
+        if (valid) {
+            uint32_t walk = (s_nz[t] | touched) & m.diffusive;
+            const uint32_t Aw = s_thr[t].w;
+            uint32_t rblk = 0xFFFFFFFFu;
+            uint4 rb = make_uint4(0, 0, 0, 0);
+            while (walk) {
+                const int s = __ffs(walk) - 1;
+                walk &= walk - 1;
+                if ((uint32_t)(((uint64_t)Aw * a.scale[s]) >> 31) == 0u) continue;  // draws nothing
+                const int32_t M = trial_count(a, s, cnt_all[s * BLOCK + t], (touched >> s) & 1u, O, tS, s_tet[t],
+                                              c0, c3, rblk, rb);
+                if (M > 0) {
+                    trial_all[s * BLOCK + t] = M;
+                    hm |= 1u << s;
+                    W += (uint32_t)M;
+                }
             }
+        }
+        // the chunk's Philox blocks: exclusive prefix of the lanes' block counts
+        const uint32_t nb = (W + 3u) >> 2;
+        uint32_t x = nb;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= d) x += y;
+        }
+        const uint32_t first = x - nb;
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31);
+        ww.tet[lane] = (int16_t)t;
+        ww.hm[lane] = hm;
+        ww.W[lane] = W;
+        ww.touched[lane] = touched;
+        ww.first[lane] = first;
+        if (lane == 31) ww.first[32] = total;
+        if (nb > 0 && first < (uint32_t)kMapCap) {
+            int s = __ffs(hm) - 1;
+            uint32_t h = hm & (hm - 1), before = 0, end = (uint32_t)trial_all[s * BLOCK + t];
+            for (uint32_t k = 0; k < nb && first + k < (uint32_t)kMapCap; ++k) {
+                while (4u * k >= end) {
+                    s = __ffs(h) - 1;
+                    h &= h - 1;
+                    before = end;
+                    end += (uint32_t)trial_all[s * BLOCK + t];
+                }
+                ww.map_own[first + k] = (uint32_t)lane | ((uint32_t)s << 5) | (k << 10);
+                ww.map_before[first + k] = before;
+            }
+        }
+        __syncwarp();
+        if (ch < (uint32_t)rchunks) continue;  // diffusion in phase 2
+        for (uint32_t item = lane; item < total; item += 32)
+            diffuse_block<BLOCK>(a, ww, item, trial_all, cnt_all, s_thr, s_nbr, s_tet, c0, c3);
+        __syncwarp();
+        if (valid) apply_remaining<BLOCK>(m, a, cnt_all, t, s_nz[t] | touched, i0);
+        __syncwarp();
+    }
+
+    // ---- phase 2: the reacting chunks' Philox blocks, spread over the block;
+    // phase 3: their tets' remaining counts
+    if (rchunks > 0) {
+        __syncthreads();
+        for (int c = 0; c < rchunks; ++c) {
+            const WarpWork &ww = wwork[c];
+            const uint32_t total = ww.first[32];
+            for (uint32_t item = tid; item < total; item += BLOCK)
+                diffuse_block<BLOCK>(a, ww, item, trial_all, cnt_all, s_thr, s_nbr, s_tet, c0, c3);
+        }
+        __syncthreads();
+        for (int c = tid >> 5; c < rchunks; c += BLOCK / 32) {
+            const int t = wwork[c].tet[lane];
+            if (t >= 0) apply_remaining<BLOCK>(m, a, cnt_all, t, s_nz[t] | wwork[c].touched[lane], i0);
         }
     }
     if (bad) atomicOr(a.err, bad);
