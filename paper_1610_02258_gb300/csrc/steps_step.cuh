@@ -68,12 +68,14 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// The waiting thread may be suspended for up to about 0.5 us per try (the
+// hint) instead of spinning, leaving the issue slots to other warps.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(500u)
         : "memory");
     return ok != 0;
 }
@@ -369,7 +371,8 @@ struct WarpWork {
 template <int BLOCK>
 __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork &ww, uint32_t item,
                                               const int32_t *trial_all, int32_t *cnt_all, const uint4 *s_thr,
-                                              const int4 *s_nbr, const uint32_t *s_tet, uint32_t c0, uint32_t c3) {
+                                              const int4 *s_nbr, const uint32_t *s_tet, const uint32_t *s_scale,
+                                              uint32_t c0, uint32_t c3) {
     int lane, s;
     uint32_t k, before;
     if (item < (uint32_t)kMapCap) {
@@ -410,7 +413,7 @@ __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork 
     const size_t Tpad = (size_t)a.Tpad;
     const uint4 rw = philox4x32_10(a.key0, a.key1, c0, s_tet[t], k, (kPurposeDiff << 28) | c3);
     uint32_t T0, T1, T2, T3;
-    species_thresholds(A, a.scale[s], T0, T1, T2, T3);
+    species_thresholds(A, s_scale[s], T0, T1, T2, T3);
     uint32_t w = 4u * k;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -419,7 +422,7 @@ __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork 
                 s = __ffs(hm) - 1;
                 hm &= hm - 1;
                 end += (uint32_t)trial_all[s * BLOCK + t];
-                species_thresholds(A, a.scale[s], T0, T1, T2, T3);
+                species_thresholds(A, s_scale[s], T0, T1, T2, T3);
             }
             const uint32_t x = word_of(rw, q) >> 1;
             if (x < T3) {
@@ -488,6 +491,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     __shared__ uint32_t next_chunk;
     __shared__ WarpWork wwork[BLOCK / 32];
     __shared__ RxnTab tb;
+    __shared__ uint32_t s_scale[kMaxSpecies];
     __shared__ __align__(8) uint64_t bar;
 
     const int S = m.S;
@@ -514,6 +518,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         mbar_init(&bar, 1);
     }
     build_rxn_tab<BLOCK>(m, tb);
+    if (tid < S) s_scale[tid] = a.scale[tid];
     __syncthreads();
     if (tid == 0) {
         const uint32_t n4 = ((uint32_t)nlive + 3u) & ~3u;
@@ -540,15 +545,23 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         __syncthreads();
         return;
     }
+    // `cur` receives the window after next: zero its non-zero entries (an
+    // immobile entry is overwritten by that window anyway)
     uint32_t nz = 0;
     if (live) {
+        int32_t vmin = 0;
+        int32_t *row = a.cur + i;
+#pragma unroll 4
         for (int s = 0; s < S; ++s) {
             const int32_t v = cnt_all[s * BLOCK + tid];
-            bad |= v < 0 ? 1u : 0u;
-            nz |= (v != 0 ? 1u : 0u) << s;
-            // a mobile entry receives the window after next: zero it (it is zero already when v == 0)
-            if (v != 0 && ((m.diffusive >> s) & 1u)) a.cur[s * Tpad + i] = 0;
+            vmin = min(vmin, v);
+            if (v != 0) {
+                nz |= 1u << s;
+                *row = 0;
+            }
+            row += Tpad;
         }
+        bad |= vmin < 0 ? 1u : 0u;
     }
     s_nz[tid] = nz;
 
@@ -563,17 +576,22 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         float a0 = 0.0f;
         // a_r = 0 (exactly: a product with a zero count) unless every reactant
         // is present; reactions no tet of the warp can fire are skipped
+        // lane r decides whether reaction r can fire in any tet of the warp
         const uint32_t wnz = __reduce_or_sync(0xFFFFFFFFu, nz);
         const uint32_t wact = __reduce_or_sync(0xFFFFFFFFu, active);
+        const uint32_t need_l = lane < m.R ? tb.need[lane] : 0u;
+        const uint32_t possible =
+            __ballot_sync(0xFFFFFFFFu, lane < m.R && ((wact >> lane) & 1u) && (wnz & need_l) == need_l);
+        if (possible) {
 #pragma unroll
-        for (int r = 0; r < RM; ++r) {
-            if (r < m.R) {
-                const uint32_t need = tb.need[r];
-                float ar = 0.0f;
-                if (((wact >> r) & 1u) && (wnz & need) == need)
-                    ar = ((active >> r) & 1u) ? propensity(tb.p[r], cnt, inv_nav, has0) : 0.0f;
-                a0 = __fadd_rn(a0, ar);
-                psum[r] = a0;
+            for (int r = 0; r < RM; ++r) {
+                if (r < m.R) {
+                    float ar = 0.0f;
+                    if ((possible >> r) & 1u)
+                        ar = ((active >> r) & 1u) ? propensity(tb.p[r], cnt, inv_nav, has0) : 0.0f;
+                    a0 = __fadd_rn(a0, ar);
+                    psum[r] = a0;
+                }
             }
         }
         if (live && a0 > 0.0f) {
@@ -628,18 +646,32 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         if (valid) {
             uint32_t walk = (s_nz[t] | touched) & m.diffusive;
             const uint32_t Aw = s_thr[t].w;
-            uint32_t rblk = 0xFFFFFFFFu;
-            uint4 rb = make_uint4(0, 0, 0, 0);
-            while (walk) {
-                const int s = __ffs(walk) - 1;
-                walk &= walk - 1;
-                if ((uint32_t)(((uint64_t)Aw * a.scale[s]) >> 31) == 0u) continue;  // draws nothing
-                const int32_t M = trial_count(a, s, cnt_all[s * BLOCK + t], (touched >> s) & 1u, O, tS, s_tet[t],
-                                              c0, c3, rblk, rb);
-                if (M > 0) {
-                    trial_all[s * BLOCK + t] = M;
-                    hm |= 1u << s;
-                    W += (uint32_t)M;
+            if (!touched || !a.occ) {
+                // no occupancy rounding: the trial count is the count
+                while (walk) {
+                    const int s = __ffs(walk) - 1;
+                    walk &= walk - 1;
+                    const int32_t M = cnt_all[s * BLOCK + t];
+                    if (M > 0 && (uint32_t)(((uint64_t)Aw * s_scale[s]) >> 31) != 0u) {
+                        trial_all[s * BLOCK + t] = M;
+                        hm |= 1u << s;
+                        W += (uint32_t)M;
+                    }
+                }
+            } else {
+                uint32_t rblk = 0xFFFFFFFFu;
+                uint4 rb = make_uint4(0, 0, 0, 0);
+                while (walk) {
+                    const int s = __ffs(walk) - 1;
+                    walk &= walk - 1;
+                    if ((uint32_t)(((uint64_t)Aw * s_scale[s]) >> 31) == 0u) continue;  // draws nothing
+                    const int32_t M = trial_count(a, s, cnt_all[s * BLOCK + t], (touched >> s) & 1u, O, tS,
+                                                  s_tet[t], c0, c3, rblk, rb);
+                    if (M > 0) {
+                        trial_all[s * BLOCK + t] = M;
+                        hm |= 1u << s;
+                        W += (uint32_t)M;
+                    }
                 }
             }
         }
@@ -676,7 +708,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         __syncwarp();
         if (ch < (uint32_t)rchunks) continue;  // diffusion in phase 2
         for (uint32_t item = lane; item < total; item += 32)
-            diffuse_block<BLOCK>(a, ww, item, trial_all, cnt_all, s_thr, s_nbr, s_tet, c0, c3);
+            diffuse_block<BLOCK>(a, ww, item, trial_all, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3);
         __syncwarp();
         if (valid) apply_remaining<BLOCK>(m, a, cnt_all, t, s_nz[t] | touched, i0);
         __syncwarp();
@@ -690,7 +722,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
             const WarpWork &ww = wwork[c];
             const uint32_t total = ww.first[32];
             for (uint32_t item = tid; item < total; item += BLOCK)
-                diffuse_block<BLOCK>(a, ww, item, trial_all, cnt_all, s_thr, s_nbr, s_tet, c0, c3);
+                diffuse_block<BLOCK>(a, ww, item, trial_all, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3);
         }
         __syncthreads();
         for (int c = tid >> 5; c < rchunks; c += BLOCK / 32) {
