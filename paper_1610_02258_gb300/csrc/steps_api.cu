@@ -139,6 +139,7 @@ struct steps_sim {
         a.tau_dn = (float)tau_k;
         if ((double)a.tau_dn > tau_k) a.tau_dn = std::nextafter(a.tau_dn, 0.0f);
         a.occ = opt.occupancy;
+        a.prefetch = 1;  // launch_step sets the distance: one resident wave
         std::memcpy(a.scale, scale, sizeof(a.scale));
         return a;
     }
@@ -445,7 +446,7 @@ static int put_counts(steps_sim *sim, int32_t s0, int32_t ns, const int32_t *cou
     scatter_to_device_order<<<(unsigned)((T + 255) / 256), 256, 0, sim->stream>>>(
         sim->d_stage, (int64_t)T, ns, sim->d_inv_perm, sim->d_cnt[sim->cur] + (size_t)s0 * Tpad, Tpad);
     if (!cuda_ok(cudaGetLastError(), "steps_set_counts: scatter")) return STEPS_ERR_CUDA;
-    // the receiving buffer of mobile species must start at zero
+    // the receiving buffer must start at zero (the step kernel writes only non-zero counts)
     if (!cuda_ok(cudaMemsetAsync(sim->d_cnt[1 - sim->cur] + (size_t)s0 * Tpad, 0, (size_t)ns * Tpad * 4,
                                  sim->stream),
                  "steps_set_counts: memset"))

@@ -12,7 +12,7 @@ namespace {
 
 template <int BLOCK, int RM, bool Z>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2)
-    step_kernel_batch(const BlockWork *__restrict__ work, const RepEntry *__restrict__ reps) {
+    step_kernel_batch(const BlockWork *__restrict__ work, const RepEntry *__restrict__ reps, int32_t prefetch) {
     __shared__ __align__(16) ModelDev t_model;
     __shared__ __align__(16) StepArgs t_args;
     __shared__ int32_t t_tile;
@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2)
     if (threadIdx.x == 0) {
         t_args.cur = e->cnt[e->parity];
         t_args.nxt = e->cnt[e->parity ^ 1u];
+        t_args.prefetch = prefetch;  // tiles ahead within the member
         t_tile = bw.tile;
     }
     __syncthreads();
@@ -52,7 +53,10 @@ int launch_batch_t(const BlockWork *work, int64_t nblocks, RepEntry *reps, int m
             return STEPS_ERR_CUDA;
         }
     }
-    step_kernel_batch<BLOCK, RM, Z><<<(unsigned)nblocks, BLOCK, smem, (cudaStream_t)stream>>>(work, reps);
+    // L2 prefetch about one resident wave ahead (the work list runs through a
+    // member's tiles in order)
+    const int32_t prefetch = resident_blocks(reinterpret_cast<const void *>(step_kernel_batch<BLOCK, RM, Z>), BLOCK, smem);
+    step_kernel_batch<BLOCK, RM, Z><<<(unsigned)nblocks, BLOCK, smem, (cudaStream_t)stream>>>(work, reps, prefetch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error(std::string("batched step kernel launch: ") + cudaGetErrorString(e));

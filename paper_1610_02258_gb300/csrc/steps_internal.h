@@ -56,8 +56,8 @@ struct ModelDev {
 
 // Arguments of one diffusion window.
 struct StepArgs {
-    int32_t *cur;                 // [S][Tpad] counts at window start; mobile entries are zeroed as read
-    int32_t *nxt;                 // [S][Tpad] counts at window end (mobile entries must be zero on entry)
+    int32_t *cur;                 // [S][Tpad] counts at window start; non-zero entries are zeroed as read
+    int32_t *nxt;                 // [S][Tpad] counts at window end (all entries must be zero on entry)
     const int4 *nbr;              // [T] face neighbours (device index), -1 = boundary
     const uint4 *thr;             // [T] cumulative face thresholds at the full window, 2^31 fixed point
     const float *inv_nav;         // [T] 1 / (N_A V_L) as float
@@ -71,6 +71,7 @@ struct StepArgs {
     double tau_k, inv_tau_k;
     float tau_dn;                 // largest float <= tau_k
     int32_t occ;                  // STEPS_OCC_*
+    int32_t prefetch;             // tiles ahead whose tables a block prefetches into L2 (0 = none)
     uint32_t scale[kMaxSpecies];  // per-species fixed-point scale for this window length
 };
 

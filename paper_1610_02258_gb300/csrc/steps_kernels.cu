@@ -1,5 +1,7 @@
 // Plain step kernel (one simulation per launch), its launchers, and the
 // device test hooks.
+#include <algorithm>
+
 #include "steps_step.cuh"
 
 namespace steps {
@@ -44,7 +46,12 @@ int launch_step_t(const ModelDev &m, const StepArgs &a, void *stream) {
             return STEPS_ERR_CUDA;
         }
     }
-    step_kernel<BLOCK, RM, Z><<<(unsigned)grid, BLOCK, smem, (cudaStream_t)stream>>>(m, a);
+    StepArgs b = a;
+    if (b.prefetch) {
+        // about one resident wave ahead
+        b.prefetch = resident_blocks(reinterpret_cast<const void *>(step_kernel<BLOCK, RM, Z>), BLOCK, smem);
+    }
+    step_kernel<BLOCK, RM, Z><<<(unsigned)grid, BLOCK, smem, (cudaStream_t)stream>>>(m, b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error(std::string("step kernel launch: ") + cudaGetErrorString(e));

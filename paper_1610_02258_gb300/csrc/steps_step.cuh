@@ -59,6 +59,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  : "memory");
 }
 
+// Prefetch into L2; bytes: multiple of 16, address 16-byte aligned.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // bytes: multiple of 16; both addresses 16-byte aligned
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
@@ -435,38 +440,61 @@ __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork 
     }
 }
 
-// What stays in tet t after diffusion is added to its own entry of nxt
-// (immobile species are written by this tet alone). `may` holds the species
-// that can be non-zero (non-zero at the start or changed by a reaction).
+// What stays in tet t after diffusion is added to its own entry of nxt. Every
+// entry of nxt is zero when the window starts (the previous window zeroed the
+// non-zero entries of this buffer as it read them; set-up zeroes it once), so
+// only non-zero counts are written: an immobile species by this tet alone, a
+// mobile one by an atomic add beside the movers from the neighbours. `may`
+// holds the species that can be non-zero (non-zero at the start or changed by
+// a reaction).
 template <int BLOCK>
 __device__ __forceinline__ void apply_remaining(const ModelDev &m, const StepArgs &a, const int32_t *cnt_all, int t,
                                                 uint32_t may, int64_t i0) {
-    const int S = m.S;
-    uint32_t out_set = (may & m.diffusive) | (~m.diffusive & ((S < 32 ? (1u << S) : 0u) - 1u));
     int32_t *out = a.nxt + i0 + t;
     const size_t Tpad = (size_t)a.Tpad;
-    while (out_set) {
-        const int s = __ffs(out_set) - 1;
-        out_set &= out_set - 1;
+    while (may) {
+        const int s = __ffs(may) - 1;
+        may &= may - 1;
         const int32_t N = cnt_all[s * BLOCK + t];
-        if ((m.diffusive >> s) & 1u) {
-            if (N) atomicAdd(out + s * Tpad, N);
-        } else {
-            out[s * Tpad] = N;
+        if (N) {
+            if ((m.diffusive >> s) & 1u) atomicAdd(out + s * Tpad, N);
+            else out[s * Tpad] = N;
         }
     }
 }
 
+// Blocks of a kernel resident on the whole GPU at once (SMs x blocks per SM),
+// cached per kernel and shared-memory size.
+__host__ inline int resident_blocks(const void *kernel, int block, size_t smem) {
+    struct Entry {
+        const void *k;
+        size_t smem;
+        int n;
+    };
+    static thread_local Entry cache[8] = {};
+    for (const Entry &e : cache)
+        if (e.k == kernel && e.smem == smem) return e.n;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+    const int n = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    static thread_local int next = 0;
+    cache[next] = Entry{kernel, smem, n};
+    next = (next + 1) & 7;
+    return n;
+}
+
 // One diffusion window for BLOCK consecutive tets (device order).
 //  load   counts and tables into shared memory by bulk copies; each thread
-//         notes its tet's non-zero species and zeroes their mobile entries
-//         in `cur` (which receives the window after next)
+//         notes its tet's non-zero species and zeroes their entries in `cur`
+//         (which receives the window after next)
 //  A      each thread: its tet's propensities (reactions no tet of the warp
 //         can fire are skipped warp-wide: their propensity is 0) and first
 //         waiting time, in float; (double)dt > tau_k is tested as
 //         dt > tau_dn, tau_dn the largest float <= tau_k (the same decision);
 //         a tet whose first event falls inside the window fires it here and
-//         is listed as reacting, the others as calm
+//         is listed as reacting, the others holding molecules as calm
 //  chunks each warp takes chunks of 32 listed tets (reacting tets first):
 //         the reacting tets' SSA from their second event on; trial counts;
 //         the chunk's Philox blocks of trial words (each word moves or keeps
@@ -531,11 +559,27 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         bulk_g2s(s_inv_nav, a.inv_nav + i0, n4 * 4u, &bar);
         if (a.orig) bulk_g2s(s_tet, a.orig + i0, n4 * 4u, &bar);
         if (a.rmask) bulk_g2s(s_mask, a.rmask + i0, n4 * 4u, &bar);
+        // the tile `prefetch` tiles ahead, processed about one resident wave
+        // later, into L2
+        const int64_t p0 = i0 + (int64_t)a.prefetch * BLOCK;
+        if (a.prefetch > 0 && p0 < a.T) {
+            const uint32_t pl = (uint32_t)min((int64_t)BLOCK, (int64_t)a.T - p0);
+            const uint32_t p4 = (pl + 3u) & ~3u;
+            for (int s = 0; s < S; ++s) bulk_prefetch_l2(a.cur + s * Tpad + p0, p4 * 4u);
+            bulk_prefetch_l2(a.thr + p0, pl * 16u);
+            bulk_prefetch_l2(a.nbr + p0, pl * 16u);
+            bulk_prefetch_l2(a.inv_nav + p0, p4 * 4u);
+            if (a.orig) bulk_prefetch_l2(a.orig + p0, p4 * 4u);
+            if (a.rmask) bulk_prefetch_l2(a.rmask + p0, p4 * 4u);
+        }
     }
     if (!a.orig) s_tet[tid] = (uint32_t)i;
     if (!a.rmask) s_mask[tid] = 0xFFFFFFFFu;
     cnt_all[S * BLOCK + tid] = 1;
-    const bool arrived = mbar_wait_bounded(&bar, 0);
+    // one thread waits for the copies (bounded) while the others sleep at the
+    // barrier; then every thread observes the completed phase itself
+    bool arrived = true;
+    if (tid == 0) arrived = mbar_wait_bounded(&bar, 0);
     if (__syncthreads_or(!arrived)) {
         // the copies did not land in time: report, let them finish (bounded), skip the window
         if (tid == 0) {
@@ -545,6 +589,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         __syncthreads();
         return;
     }
+    mbar_try_wait(&bar, 0);  // completed: returns at once
     // `cur` receives the window after next: zero its non-zero entries (an
     // immobile entry is overwritten by that window anyway)
     uint32_t nz = 0;
@@ -610,9 +655,21 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
             }
         }
     }
-    if (live) {
-        if (reacting) list[atomicAdd(&nreact, 1)] = (int16_t)tid;
-        else list[BLOCK - 1 - atomicAdd(&ncalm, 1)] = (int16_t)tid;
+    {
+        // warp-aggregated list appends: one atomic per warp and list
+        // a calm tet with no molecules has nothing to do this window
+        const uint32_t rmask = __ballot_sync(0xFFFFFFFFu, live && reacting);
+        const uint32_t cmask = __ballot_sync(0xFFFFFFFFu, live && !reacting && nz != 0u);
+        int rbase = 0, cbase = 0;
+        if (lane == 0) {
+            if (rmask) rbase = atomicAdd(&nreact, __popc(rmask));
+            if (cmask) cbase = atomicAdd(&ncalm, __popc(cmask));
+        }
+        rbase = __shfl_sync(0xFFFFFFFFu, rbase, 0);
+        cbase = __shfl_sync(0xFFFFFFFFu, cbase, 0);
+        const uint32_t below = (1u << lane) - 1u;
+        if ((rmask >> lane) & 1u) list[rbase + __popc(rmask & below)] = (int16_t)tid;
+        else if ((cmask >> lane) & 1u) list[BLOCK - 1 - (cbase + __popc(cmask & below))] = (int16_t)tid;
     }
     __syncthreads();
 
@@ -620,8 +677,8 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     // ones), one warp each. The reacting chunks run their SSA and trial counts
     // and leave their diffusion to phase 2; calm chunks finish here.
     const int nr = nreact, nc = ncalm;
-    const int rchunks = (nr + 31) >> 5;
     const int nchunks = (nr + nc + 31) >> 5;
+    const int rchunks = (nr + 31) >> 5;
     for (;;) {
         uint32_t ch = 0;
         if (lane == 0) ch = atomicAdd(&next_chunk, 1u);
