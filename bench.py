@@ -129,7 +129,24 @@ def profile_traffic(name: str):
         return None
     if kv.get("kernel_sources_sha256_16", "").strip() != kernel_sources_hash():
         return None
-    return {k.strip(): int(v) for k, v in kv.items() if k.strip().endswith("bytes") or k.strip() == "bytes_per_launch"}
+    return {k.strip(): int(v) for k, v in kv.items() if k.strip() != "kernel_sources_sha256_16"}
+
+
+def issue_roofline(tr, kernel_s: float, sm_mhz):
+    """Warp instructions issued per second by the kernel (count per launch from
+    the ncu capture, time per launch measured here) against the issue peak:
+    SMs x 4 schedulers x 1 warp instruction per cycle x the SM clock sampled
+    during the run."""
+    if not tr or "warp_instructions_per_launch" not in tr:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    peak = sms * 4 * mhz * 1e6
+    achieved = tr["warp_instructions_per_launch"] / kernel_s
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp-inst/s", "frac": achieved / peak,
+            "warp_instructions_per_launch": tr["warp_instructions_per_launch"], "sm_mhz": mhz,
+            "note": "instruction count from the ncu capture in profiles/, time from this run"}
 
 
 def replica_seed(rank: int) -> int:
@@ -252,11 +269,12 @@ def measure_dendrite(args, capi, I, torch, peak):
     achieved = w.n_tets * bytes_per_tet / kernel_s / 1e9
     tr = profile_traffic("step_kernel_dendrite")
     out = {"value": w.n_tets * windows / (ms / 1e3), "unit": UNIT, "workload": w.name, "tets": w.n_tets,
+           "form": "plain",
            "species": S, "reactions": w.model.n_reac, "tau_us": sim.tau * 1e6, "sim_ms_per_step": args.dendrite_ms,
            "windows_per_step": windows / steps, "ms_per_step": ms / steps, "steps": steps,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": tr["bytes_per_launch"] if tr else None, "bytes_per_tet_update": bytes_per_tet,
-                        "kernel_us_avg": kernel_s * 1e6},
+                        "kernel_us_avg": kernel_s * 1e6, "issue": issue_roofline(tr, kernel_s, None)},
            "setup_s": setup_s, "l2": "working set > L2; also flushed before each step"}
     sim.close()
     return out
@@ -413,7 +431,8 @@ def run_ours(args):
         "gpu_launches": int(l1 - l0),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": peak_kind,
-                     "bytes_per_tet_update": bytes_per_tet, "kernel_us_avg": kernel_s * 1e6},
+                     "bytes_per_tet_update": bytes_per_tet, "kernel_us_avg": kernel_s * 1e6,
+                     "issue": issue_roofline(tr, kernel_s, clk["sm_mhz"] if clk else None)},
         "clocks": clk,
     }
     if world == 1 and not args.no_forms and args.workload == "irregular-box":

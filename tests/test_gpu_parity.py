@@ -111,6 +111,20 @@ def test_full_size_config2_whole_run_bit_exact(capi):
     assert np.array_equal(gc, oc)
 
 
+def test_full_size_dendrite_bit_exact(capi):
+    """The dendrite workload at full size (1,034,502 tets, 20 species, influx
+    masked to the soma end: the order-0 kernel variant), 20 windows plus a
+    shortened one, in the launch configuration the benchmark times."""
+    w = I.config3()
+    assert w.n_tets > 1_000_000
+    g = capi.from_workload(w)
+    t_end = 20.5 * g.tau
+    gc, oc, g2, o = run_both(capi, w.verts, w.tets, w.model, w.counts, w.seed, t_end, masks=w.reac_masks)
+    assert g2.windows == 21
+    assert o.events > 0
+    assert np.array_equal(gc, oc)
+
+
 def test_region_mask_and_zero_order_influx_bit_exact(capi):
     """Reaction masks (influx only in the first 5% of tets) on a small
     dendrite-shaped mesh with the 20-species calcium network."""
