@@ -157,6 +157,39 @@ int steps_set_reac_mask(steps_sim *sim, int32_t reac, const uint8_t *active);
  */
 int steps_run(steps_sim *sim, double t_end);
 
+/*
+ * Set the rate constant of reaction `reac` (SI units as in
+ * steps_model_create) for the windows that follow. The paper drives its
+ * calcium-burst runs with influx rates that change over time per region
+ * (§3.2); a caller changes the rate between steps_run calls (or between
+ * recording runs) to follow such a profile. The kernels use (float)k.
+ * Errors: STEPS_ERR_ARG for a reaction out of range or a rate that is
+ * negative or not finite. The next run re-captures its CUDA graphs.
+ */
+int steps_set_reac_rate(steps_sim *sim, int32_t reac, double k);
+
+/*
+ * Advance to t_end like steps_run and record, at every time t0 + k dt_rec
+ * (k = 1, 2, ... while <= t_end; t0 = the time at the call; times
+ * recomputed, not accumulated), the counts of n_species species (indices
+ * `species`) at n_tets tets (original ids `tets`) into d_out, the way the
+ * paper records concentrations at fixed intervals (§3.2). Each recording
+ * time is a window boundary: the run stops there like steps_run(t) would
+ * (a shortened window when dt_rec is not a multiple of tau), so the
+ * recorded counts equal those of successive steps_run calls, bit for bit.
+ * d_out: caller-owned DEVICE memory of at least max_records * n_species *
+ * n_tets int32, recording k - 1 at offset (k - 1) n_species n_tets, laid
+ * out [species][tet] in the order given. The snapshots are taken on the
+ * device with no host synchronisation between them; the call synchronises
+ * once at the end. *n_records (may be NULL) receives the number written.
+ * The selection is copied to a small device buffer the simulation keeps.
+ * Errors: STEPS_ERR_ARG for bad species/tet indices, a non-positive dt_rec
+ * or more recordings than max_records (checked before anything runs); the
+ * errors of steps_run otherwise.
+ */
+int steps_run_record(steps_sim *sim, double t_end, double dt_rec, int32_t n_species, const int32_t *species,
+                     int32_t n_tets, const int32_t *tets, int32_t *d_out, int64_t max_records, int64_t *n_records);
+
 int steps_get_time(const steps_sim *sim, double *t);
 int steps_get_tau(const steps_sim *sim, double *tau);
 /* Windows run so far (the RNG window index) and kernel launches issued. */

@@ -38,6 +38,8 @@ def lib():
         L.orc_set_counts.argtypes = [P, ctypes.c_int, P]
         L.orc_get_counts.argtypes = [P, ctypes.c_int, P]
         L.orc_set_reac_mask.argtypes = [P, ctypes.c_int, P]
+        L.orc_set_reac_rate.argtypes = [P, ctypes.c_int, ctypes.c_double]
+        L.orc_set_reac_rate.restype = ctypes.c_int
         L.orc_run.argtypes = [P, ctypes.c_double]
         L.orc_run.restype = ctypes.c_int
         L.orc_step.argtypes = [P, ctypes.c_double]
@@ -165,6 +167,10 @@ class OracleSim:
         else:
             m = np.ascontiguousarray(mask, np.uint8)
             lib().orc_set_reac_mask(self._h, r, _p(m))
+
+    def set_reac_rate(self, r, k):
+        if lib().orc_set_reac_rate(self._h, int(r), float(k)) != 0:
+            raise ValueError("oracle: bad reaction or rate")
 
     def get_counts(self):
         out = np.empty((self.S, self.nt), np.int32)

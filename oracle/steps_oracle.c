@@ -382,6 +382,15 @@ void orc_set_reac_mask(orc_sim *s, int r, const uint8_t *m)
     else s->has_mask[r] = 0;
 }
 
+/* Rate constant of reaction r from the next window on: the paper drives its
+   calcium-burst runs with influx rates that change over time (§3.2). */
+int orc_set_reac_rate(orc_sim *s, int r, double k)
+{
+    if (r < 0 || r >= s->R || !(k >= 0.0) || k != k || k - k != 0.0) return ORC_ERR_MODEL;
+    s->k[r] = k;
+    return 0;
+}
+
 double orc_get_tau(const orc_sim *s) { return s->tau; }
 int64_t orc_get_events(const orc_sim *s) { return s->events; }
 uint64_t orc_get_windows(const orc_sim *s) { return s->k_total; }

@@ -30,7 +30,7 @@ EXPORTS = [
     "steps_set_reac_mask", "steps_run", "steps_get_time", "steps_get_tau", "steps_get_windows",
     "steps_last_error", "steps_debug_philox", "steps_debug_logf", "steps_run_noalloc",
     "steps_batch_options_default", "steps_batch_create", "steps_batch_destroy", "steps_batch_run",
-    "steps_batch_info", "steps_sim_clone", "steps_sim_device_bytes",
+    "steps_batch_info", "steps_sim_clone", "steps_sim_device_bytes", "steps_set_reac_rate", "steps_run_record",
 ]
 
 
@@ -85,6 +85,9 @@ def _load():
                                             ctypes.POINTER(ctypes.c_float)]),
         "steps_sim_clone": (ctypes.c_int, [P, u64, P, PP]),
         "steps_sim_device_bytes": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "steps_set_reac_rate": (ctypes.c_int, [P, i32, ctypes.c_double]),
+        "steps_run_record": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_double, i32, P, i32, P, P, i64,
+                                            ctypes.POINTER(ctypes.c_int64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -210,6 +213,21 @@ def steps_run_noalloc(sim, d_counts_ptr, t_end):
     """Advance on caller-owned device counts (an int pointer to [S * nt] int32,
     species-major, original tet order), allocating nothing."""
     _check(lib.steps_run_noalloc(sim, ctypes.c_void_p(int(d_counts_ptr)), float(t_end)))
+
+
+def steps_set_reac_rate(sim, reac, k):
+    _check(lib.steps_set_reac_rate(sim, int(reac), float(k)))
+
+
+def steps_run_record(sim, t_end, dt_rec, species, tets, d_out_ptr, max_records):
+    """Records into caller-owned device memory at d_out_ptr (int32,
+    [max_records][len(species)][len(tets)]); returns the number of recordings."""
+    sp = np.ascontiguousarray(species, np.int32)
+    tt = np.ascontiguousarray(tets, np.int32)
+    n = ctypes.c_int64(0)
+    _check(lib.steps_run_record(sim, float(t_end), float(dt_rec), sp.size, _ptr(sp), tt.size, _ptr(tt),
+                                ctypes.c_void_p(d_out_ptr), int(max_records), ctypes.byref(n)))
+    return n.value
 
 
 def steps_get_time(sim):
@@ -353,6 +371,12 @@ class Simulation:
 
     def get_counts(self, out=None):
         return steps_get_counts_all(self._sim, self.S, self.nt, out)
+
+    def set_reac_rate(self, r, k):
+        steps_set_reac_rate(self._sim, r, k)
+
+    def run_record(self, t_end, dt_rec, species, tets, d_out_ptr, max_records):
+        return steps_run_record(self._sim, t_end, dt_rec, species, tets, d_out_ptr, max_records)
 
     def set_reac_mask(self, r, mask):
         steps_set_reac_mask(self._sim, r, mask)

@@ -83,6 +83,8 @@ struct steps_sim {
     uint32_t *d_err = nullptr;
     uint64_t *d_window_base = nullptr;
     int32_t *d_stage = nullptr;     // [S * nt] original-order staging
+    int32_t *d_rec = nullptr;       // recording selection (species, then tets)
+    size_t rec_bytes = 0;
     // time
     double t_base = 0.0;
     int64_t k_grid = 0;
@@ -108,6 +110,7 @@ struct steps_sim {
         cudaFree(d_err);
         cudaFree(d_window_base);
         cudaFree(d_stage);
+        cudaFree(d_rec);
     }
 
     void drop_graphs() {
@@ -536,12 +539,13 @@ int steps_set_reac_mask(steps_sim *sim, int32_t reac, const uint8_t *active) {
     return STEPS_OK;
 }
 
-int steps_run(steps_sim *sim, double t_end) {
-    CHECK_NULL(sim, "steps_run");
-    if (!std::isfinite(t_end)) {
-        set_error("steps_run: t_end must be finite");
-        return STEPS_ERR_ARG;
-    }
+}  // extern "C"
+
+namespace {
+
+// Enqueues the windows of Algorithm 1 from the simulation's time to t_end
+// (full windows of tau, then a shortened last window); no synchronisation.
+int enqueue_run(steps_sim *sim, double t_end) {
     const double tau = sim->tab.tau;
     const bool finite = std::isfinite(tau);
     const double tol = finite ? 1e-9 * tau : 0.0;
@@ -568,21 +572,137 @@ int steps_run(steps_sim *sim, double t_end) {
             break;
         }
     }
+    return STEPS_OK;
+}
+
+// Waits for the simulation's stream and turns the device error word into a
+// return code (and clears it).
+int finish_run(steps_sim *sim, const char *who) {
     uint32_t err = 0;
-    if (!cuda_ok(cudaMemcpyAsync(&err, sim->d_err, 4, cudaMemcpyDeviceToHost, sim->stream), "steps_run: error word") ||
-        !cuda_ok(cudaStreamSynchronize(sim->stream), "steps_run"))
+    if (!cuda_ok(cudaMemcpyAsync(&err, sim->d_err, 4, cudaMemcpyDeviceToHost, sim->stream), "error word") ||
+        !cuda_ok(cudaStreamSynchronize(sim->stream), who))
         return STEPS_ERR_CUDA;
     if (err) {
         cudaMemsetAsync(sim->d_err, 0, 4, sim->stream);
         if (err & 4u) {
-            set_error("steps_run: a bulk copy into shared memory did not complete within its wait limit");
+            set_error(std::string(who) + ": a bulk copy into shared memory did not complete within its wait limit");
             return STEPS_ERR_TIMEOUT;
         }
-        set_error(err & 2u ? "steps_run: a tet fired more than 2^24 reactions in one window (rates too large)"
-                           : "steps_run: a negative count was seen on the device");
+        set_error(std::string(who) + (err & 2u ? ": a tet fired more than 2^24 reactions in one window (rates too large)"
+                                               : ": a negative count was seen on the device"));
         return STEPS_ERR_STATE;
     }
     return STEPS_OK;
+}
+
+// One recording: counts of the chosen species (rows of cur) at the chosen
+// tets (device indices) into out[species][tet].
+__global__ void gather_record(const int32_t *cur, size_t Tpad, const int32_t *species, int32_t ns,
+                              const int32_t *tets, int32_t nr, int32_t *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ns * nr) return;
+    const int32_t q = (int32_t)(i / nr), j = (int32_t)(i % nr);
+    out[i] = cur[(size_t)species[q] * Tpad + tets[j]];
+}
+
+}  // namespace
+
+extern "C" {
+
+int steps_run(steps_sim *sim, double t_end) {
+    CHECK_NULL(sim, "steps_run");
+    if (!std::isfinite(t_end)) {
+        set_error("steps_run: t_end must be finite");
+        return STEPS_ERR_ARG;
+    }
+    int rc = enqueue_run(sim, t_end);
+    return rc ? rc : finish_run(sim, "steps_run");
+}
+
+int steps_set_reac_rate(steps_sim *sim, int32_t reac, double k) {
+    CHECK_NULL(sim, "steps_set_reac_rate");
+    if (reac < 0 || reac >= sim->model.R) {
+        set_error("steps_set_reac_rate: reaction out of range");
+        return STEPS_ERR_ARG;
+    }
+    if (!(k >= 0.0) || !std::isfinite(k)) {
+        set_error("steps_set_reac_rate: rate constant must be finite and >= 0");
+        return STEPS_ERR_ARG;
+    }
+    sim->model.k[(size_t)reac] = k;
+    sim->model.dev.reac[reac].k = (float)k;
+    sim->drop_graphs();  // the captured launches hold the old model
+    return STEPS_OK;
+}
+
+int steps_run_record(steps_sim *sim, double t_end, double dt_rec, int32_t n_species, const int32_t *species,
+                     int32_t n_tets, const int32_t *tets, int32_t *d_out, int64_t max_records, int64_t *n_records) {
+    CHECK_NULL(sim, "steps_run_record");
+    CHECK_NULL(species, "steps_run_record");
+    CHECK_NULL(tets, "steps_run_record");
+    CHECK_NULL(d_out, "steps_run_record");
+    if (n_records) *n_records = 0;
+    if (!std::isfinite(t_end) || !(dt_rec > 0.0) || !std::isfinite(dt_rec)) {
+        set_error("steps_run_record: t_end must be finite and dt_rec finite and > 0");
+        return STEPS_ERR_ARG;
+    }
+    if (n_species < 1 || n_species > sim->S || n_tets < 1 || max_records < 0) {
+        set_error("steps_run_record: bad species or tet count");
+        return STEPS_ERR_ARG;
+    }
+    for (int32_t q = 0; q < n_species; ++q)
+        if (species[q] < 0 || species[q] >= sim->S) {
+            set_error("steps_run_record: species out of range");
+            return STEPS_ERR_ARG;
+        }
+    std::vector<int32_t> dev_tets((size_t)n_tets);
+    for (int32_t j = 0; j < n_tets; ++j) {
+        if (tets[j] < 0 || tets[j] >= sim->T) {
+            set_error("steps_run_record: tet out of range");
+            return STEPS_ERR_ARG;
+        }
+        dev_tets[(size_t)j] = sim->tab.inv_perm.empty() ? tets[j] : sim->tab.inv_perm[(size_t)tets[j]];
+    }
+    // recording times t0 + k dt_rec, k = 1, 2, ... up to t_end (recomputed, not accumulated)
+    const double t0 = sim->time();
+    const double tol = 1e-12 * std::max(std::fabs(t_end), dt_rec);
+    int64_t nrec = 0;
+    while (t0 + (double)(nrec + 1) * dt_rec <= t_end + tol) ++nrec;
+    if (nrec > max_records) {
+        set_error("steps_run_record: " + std::to_string(nrec) + " recordings do not fit max_records = " +
+                  std::to_string(max_records));
+        return STEPS_ERR_ARG;
+    }
+    // the selection, uploaded once
+    const size_t need = ((size_t)n_species + (size_t)n_tets) * 4;
+    if (sim->rec_bytes < need) {
+        cudaFree(sim->d_rec);
+        sim->d_rec = nullptr;
+        sim->rec_bytes = 0;
+        if (!cuda_ok(cudaMalloc((void **)&sim->d_rec, need), "steps_run_record: alloc")) return STEPS_ERR_OOM;
+        sim->rec_bytes = need;
+    }
+    int32_t *d_species = sim->d_rec, *d_tets = sim->d_rec + n_species;
+    if (!cuda_ok(cudaMemcpyAsync(d_species, species, (size_t)n_species * 4, cudaMemcpyHostToDevice, sim->stream),
+                 "steps_run_record: upload") ||
+        !cuda_ok(cudaMemcpyAsync(d_tets, dev_tets.data(), (size_t)n_tets * 4, cudaMemcpyHostToDevice, sim->stream),
+                 "steps_run_record: upload"))
+        return STEPS_ERR_CUDA;
+    const int64_t per = (int64_t)n_species * n_tets;
+    const unsigned grid = (unsigned)((per + 255) / 256);
+    for (int64_t k = 1; k <= nrec; ++k) {
+        int rc = enqueue_run(sim, t0 + (double)k * dt_rec);
+        if (rc) return rc;
+        gather_record<<<grid, 256, 0, sim->stream>>>(sim->d_cnt[sim->cur], (size_t)sim->Tpad, d_species, n_species,
+                                                     d_tets, n_tets, d_out + (k - 1) * per);
+        if (!cuda_ok(cudaGetLastError(), "steps_run_record: gather")) return STEPS_ERR_CUDA;
+        ++sim->launches;
+    }
+    int rc = enqueue_run(sim, t_end);
+    if (!rc) rc = finish_run(sim, "steps_run_record");
+    // the host copy of dev_tets must outlive the async upload: finish_run synchronised
+    if (n_records) *n_records = rc ? 0 : nrec;
+    return rc;
 }
 
 int steps_get_time(const steps_sim *sim, double *t) {

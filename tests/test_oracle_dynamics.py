@@ -306,3 +306,32 @@ def test_reaction_only_model_one_window_per_run():
     sim.run(1e-3)
     sim.run(4e-3)
     assert sim.windows == 2 and sim.time == 4e-3
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_rate_change_gives_the_piecewise_poisson_law(prec):
+    """Zero-order influx 0 -> A into isolated tets, no diffusion (each run is
+    one exact SSA window): with rate k1 on [0, t1] and k2 on [t1, t2] the
+    count at t2 is Poisson(N_A V (k1 t1 + k2 (t2 - t1))) (a Poisson process
+    with a piecewise-constant rate). Ignoring the change (rate k1 throughout)
+    predicts a mean 3x smaller on the second piece and fails the test."""
+    n, k1, k2, t1, t2 = 4000, 2e-3, 6e-3, 1e-3, 2.5e-3
+    verts, tets = I.isolated_tets(n)
+    m = I.model_from_lists(["A"], [0.0], [([], ["A"], k1)])
+    sim = _sim(verts, tets, m, np.zeros((1, n), np.int32), 31, OCC, prec)
+    vol_l = (0.5e-6) ** 3 / 6.0 * 1e3  # a Kuhn tet of a 0.5 um cube, in litres
+    nav = 6.02214076e23 * vol_l
+    sim.run(t1)
+    sim.set_reac_rate(0, k2)
+    sim.run(t2)
+    assert sim.windows == 2
+    a = sim.get_counts()[0]
+    lam = nav * (k1 * t1 + k2 * (t2 - t1))
+    lam_wrong = nav * k1 * t2
+    ks = np.arange(a.max() + 1)
+    pmf = stats.poisson.pmf(ks, lam)
+    pmf[-1] += stats.poisson.sf(ks[-1], lam)
+    assert chi2_pvalue(a, ks, pmf) > 1e-3
+    se = math.sqrt(lam / n)
+    assert abs(a.mean() - lam) < 4 * se
+    assert abs(a.mean() - lam_wrong) > 20 * se
