@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -280,6 +281,52 @@ def measure_dendrite(args, capi, I, torch, peak):
     return out
 
 
+def measure_dendrite_recording(args, capi, I, torch):
+    """Dendrite with a time-varying influx and recording: the influx rate
+    follows a synthetic burst train, changed every 1 ms of simulated time
+    (k = k0 (1 + 4 exp(-(t mod 5 ms) / 1 ms))); Ca is recorded every 20 us at
+    1% of the tets (device-side snapshots). One step = 2 ms of simulated time."""
+    w = I.config3()
+    stream = torch.cuda.current_stream()
+    sim = capi.from_workload(w, cuda_stream=stream.cuda_stream)
+    influx = w.model.n_reac - 1
+    k0 = float(w.model.k[influx])
+    rng = np.random.default_rng(7)
+    rec_tets = np.sort(rng.choice(w.n_tets, w.n_tets // 100, replace=False)).astype(np.int32)
+    rec_species = np.array([w.model.names.index("Ca")], np.int32)
+    dt_rec, seg = 20e-6, 1e-3
+    per_seg = int(seg / dt_rec + 1e-9)
+    buf = torch.empty((per_seg, 1, rec_tets.size), dtype=torch.int32, device="cuda")
+
+    def step():
+        n = 0
+        for _ in range(2):
+            t = sim.time
+            sim.set_reac_rate(influx, k0 * (1.0 + 4.0 * math.exp(-((t % 5e-3) / 1e-3))))
+            n += sim.run_record(t + seg, dt_rec, rec_species, rec_tets, buf.data_ptr(), per_seg)
+        return n
+
+    step()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    w0, _ = capi.steps_get_windows(sim._sim)
+    steps = 3
+    t0 = time.perf_counter()
+    nrec = 0
+    for _ in range(steps):
+        nrec += step()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    w1, _ = capi.steps_get_windows(sim._sim)
+    out = {"value": w.n_tets * (w1 - w0) / wall, "unit": UNIT, "workload": w.name, "form": "plain",
+           "timing": "wall clock (host-driven rate changes and recordings)",
+           "sim_ms_per_step": 2.0, "windows_per_step": (w1 - w0) / steps, "recordings_per_step": nrec / steps,
+           "recorded_tets": int(rec_tets.size), "dt_rec_us": dt_rec * 1e6, "rate_segment_ms": seg * 1e3,
+           "ms_per_step": 1e3 * wall / steps}
+    sim.close()
+    return out
+
+
 def measure_served(args, capi, I):
     """Served form: Poisson stream (50 jobs/s) of jobs from the config 1-3
     generators, 2k-1M tets, t_end 1-100 ms, admitted by a device-memory budget,
@@ -438,6 +485,8 @@ def run_ours(args):
     if world == 1 and not args.no_forms and args.workload == "irregular-box":
         line["forms"] = {"plain": {"value": value, "unit": UNIT, "workload": w.name},
                          "plain_dendrite": measure_dendrite(args, capi, I, torch, peak) if args.dendrite_ms > 0 else None,
+                         "dendrite_influx_recording": (measure_dendrite_recording(args, capi, I, torch)
+                                                       if args.dendrite_ms > 0 else None),
                          "batched": measure_batched(args, capi, I, torch, peak) if args.batch_replicates > 0 else None,
                          "served": measure_served(args, capi, I) if args.served_jobs > 0 else None}
     if world == 1 and not args.no_cpu_baseline:
