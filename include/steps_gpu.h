@@ -62,7 +62,10 @@ typedef struct steps_options {
     int32_t reorder;     /* STEPS_REORDER_* */
     int32_t block;       /* threads per block of the step kernel; 0 = default (256) */
     int32_t use_graph;   /* 1 = replay full windows from a captured CUDA graph (default), 0 = plain launches */
-    int32_t reserved[4]; /* set to 0 */
+    int32_t specialize;  /* step kernel compiled for this model at run time (NVRTC): 0 = when the mesh has at
+                            least 65,536 tets and NVRTC is available (default), 1 = always (sim creation fails
+                            with STEPS_ERR_CUDA if it cannot be built), -1 = never (the generic kernel) */
+    int32_t reserved[3]; /* set to 0 */
 } steps_options;
 
 /* Fill *opt with the defaults. */
@@ -189,6 +192,11 @@ int steps_set_reac_rate(steps_sim *sim, int32_t reac, double k);
  */
 int steps_run_record(steps_sim *sim, double t_end, double dt_rec, int32_t n_species, const int32_t *species,
                      int32_t n_tets, const int32_t *tets, int32_t *d_out, int64_t max_records, int64_t *n_records);
+
+/* *specialized = 1 when the simulation runs a step kernel compiled for its
+ * model (see steps_options.specialize), else 0. The two kernels give the same
+ * results bit for bit; the specialised one takes fewer instructions. */
+int steps_sim_specialized(const steps_sim *sim, int32_t *specialized);
 
 int steps_get_time(const steps_sim *sim, double *t);
 int steps_get_tau(const steps_sim *sim, double *tau);

@@ -31,6 +31,7 @@ EXPORTS = [
     "steps_last_error", "steps_debug_philox", "steps_debug_logf", "steps_run_noalloc",
     "steps_batch_options_default", "steps_batch_create", "steps_batch_destroy", "steps_batch_run",
     "steps_batch_info", "steps_sim_clone", "steps_sim_device_bytes", "steps_set_reac_rate", "steps_run_record",
+    "steps_sim_specialized",
 ]
 
 
@@ -42,7 +43,7 @@ class StepsError(RuntimeError):
 
 class steps_options(ctypes.Structure):
     _fields_ = [("occupancy", ctypes.c_int32), ("reorder", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("use_graph", ctypes.c_int32), ("specialize", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class steps_batch_options(ctypes.Structure):
@@ -86,6 +87,7 @@ def _load():
         "steps_sim_clone": (ctypes.c_int, [P, u64, P, PP]),
         "steps_sim_device_bytes": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64)]),
         "steps_set_reac_rate": (ctypes.c_int, [P, i32, ctypes.c_double]),
+        "steps_sim_specialized": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
         "steps_run_record": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_double, i32, P, i32, P, P, i64,
                                             ctypes.POINTER(ctypes.c_int64)]),
     }
@@ -230,6 +232,12 @@ def steps_run_record(sim, t_end, dt_rec, species, tets, d_out_ptr, max_records):
     return n.value
 
 
+def steps_sim_specialized(sim):
+    v = ctypes.c_int32(0)
+    _check(lib.steps_sim_specialized(sim, ctypes.byref(v)))
+    return bool(v.value)
+
+
 def steps_get_time(sim):
     t = ctypes.c_double()
     _check(lib.steps_get_time(sim, ctypes.byref(t)))
@@ -325,7 +333,7 @@ class Simulation:
     the calls above; counts are [S, nt] numpy arrays in the caller's tet order)."""
 
     def __init__(self, verts, tets, model, seed, occupancy=STEPS_OCC_MEAN, reorder=STEPS_REORDER_MORTON,
-                 block=256, use_graph=True, cuda_stream=None):
+                 block=256, use_graph=True, cuda_stream=None, specialize=0):
         self.S = model.n_species
         self.R = model.n_reac
         self.nt = int(np.asarray(tets).shape[0])
@@ -336,6 +344,7 @@ class Simulation:
         opt.reorder = reorder
         opt.block = block
         opt.use_graph = 1 if use_graph else 0
+        opt.specialize = int(specialize)
         self._sim = steps_sim_create(self._mesh, self._model, seed, opt, cuda_stream)
 
     def clone(self, seed, cuda_stream=None):
@@ -391,6 +400,10 @@ class Simulation:
     @property
     def tau(self):
         return steps_get_tau(self._sim)
+
+    @property
+    def specialized(self):
+        return steps_sim_specialized(self._sim)
 
     @property
     def windows(self):

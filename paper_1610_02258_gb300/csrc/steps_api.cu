@@ -85,6 +85,8 @@ struct steps_sim {
     int32_t *d_stage = nullptr;     // [S * nt] original-order staging
     int32_t *d_rec = nullptr;       // recording selection (species, then tets)
     size_t rec_bytes = 0;
+    void *spec = nullptr;           // step kernel compiled for this model (cached process-wide), or null
+    std::string spec_why;           // why there is none
     // time
     double t_base = 0.0;
     int64_t k_grid = 0;
@@ -147,11 +149,16 @@ struct steps_sim {
         return a;
     }
 
+    // one window on the model-specialised kernel if there is one, else the generic one
+    int launch(const StepArgs &a, cudaStream_t st) const {
+        return spec ? launch_spec(spec, model.dev, a, opt.block, st) : launch_step(model.dev, a, opt.block, st);
+    }
+
     int window_launch(double tau_k) {  // one window of explicit length, plain launch
         uint32_t scale[kMaxSpecies] = {};
         for (int s = 0; s < S; ++s) scale[s] = species_scale(model, tab, s, tau_k);
         StepArgs a = args(cur, k_total, nullptr, tau_k, scale);
-        int rc = launch_step(model.dev, a, opt.block, stream);
+        int rc = launch(a, stream);
         if (rc) return rc;
         ++launches;
         cur = 1 - cur;
@@ -171,7 +178,7 @@ struct steps_sim {
         int b = from;
         for (int q = 0; q < kGraphWindows && rc == STEPS_OK; ++q) {
             StepArgs a = args(b, (uint64_t)q, d_window_base, tab.tau, scale_full);
-            rc = launch_step(model.dev, a, opt.block, cs);
+            rc = launch(a, cs);
             b = 1 - b;
         }
         if (rc == STEPS_OK) rc = launch_add_u64(d_window_base, kGraphWindows, cs);
@@ -203,7 +210,7 @@ struct steps_sim {
         }
         for (; done < n; ++done) {
             StepArgs a = args(cur, k_total, nullptr, tab.tau, scale_full);
-            int rc = launch_step(model.dev, a, opt.block, stream);
+            int rc = launch(a, stream);
             if (rc) return rc;
             ++launches;
             cur = 1 - cur;
@@ -232,6 +239,7 @@ void steps_options_default(steps_options *opt) {
     opt->reorder = STEPS_REORDER_MORTON;
     opt->block = 256;
     opt->use_graph = 1;
+    opt->specialize = 0;
 }
 
 int steps_mesh_create(const double *verts_xyz, int64_t nv, const int32_t *tets, int64_t nt, steps_mesh **out) {
@@ -361,6 +369,17 @@ int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t 
              cuda_ok(cudaMemcpy(s->d_inv_perm, s->tab.inv_perm.data(), T * 4, cudaMemcpyHostToDevice),
                      "upload inv_perm");
     if (!ok) return STEPS_ERR_CUDA;
+    // the model-specialised step kernel (compiled once per model and block size)
+    constexpr int64_t kSpecializeMinTets = 65536;
+    if (s->opt.specialize > 0 || (s->opt.specialize == 0 && s->T >= kSpecializeMinTets)) {
+        s->spec = spec_kernel(s->model, s->opt.block, &s->spec_why);
+        if (!s->spec && s->opt.specialize > 0) {
+            set_error("steps_sim_create: the specialised step kernel could not be built: " + s->spec_why);
+            return STEPS_ERR_CUDA;
+        }
+    } else {
+        s->spec_why = "not requested";
+    }
     *out = s.release();
     return STEPS_OK;
 }
@@ -383,6 +402,8 @@ int steps_sim_clone(const steps_sim *src, uint64_t seed, void *cuda_stream, step
     s->S = src->S;
     s->seed = seed;
     s->h_rmask = src->h_rmask;
+    s->spec = src->spec;
+    s->spec_why = src->spec_why;
     std::memcpy(s->scale_full, src->scale_full, sizeof(s->scale_full));
     const size_t Tpad = (size_t)s->Tpad, S = (size_t)s->S, T = (size_t)s->T;
     cudaError_t e = cudaSuccess;
@@ -703,6 +724,13 @@ int steps_run_record(steps_sim *sim, double t_end, double dt_rec, int32_t n_spec
     // the host copy of dev_tets must outlive the async upload: finish_run synchronised
     if (n_records) *n_records = rc ? 0 : nrec;
     return rc;
+}
+
+int steps_sim_specialized(const steps_sim *sim, int32_t *specialized) {
+    CHECK_NULL(sim, "steps_sim_specialized");
+    CHECK_NULL(specialized, "steps_sim_specialized");
+    *specialized = sim->spec ? 1 : 0;
+    return STEPS_OK;
 }
 
 int steps_get_time(const steps_sim *sim, double *t) {
@@ -1174,7 +1202,7 @@ extern "C" int steps_run_noalloc(steps_sim *sim, int32_t *d_counts, double t_end
         a.cur = buf[cur];
         a.nxt = buf[1 - cur];
         a.err = sc.err;
-        int r = launch_step(sim->model.dev, a, sim->opt.block, st);
+        int r = sim->launch(a, st);
         if (r) return r;
         ++sim->launches;
         ++sim->k_total;

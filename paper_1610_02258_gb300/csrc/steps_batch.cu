@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2)
         t_tile = bw.tile;
     }
     __syncthreads();
-    step_tile<BLOCK, RM, Z>(t_model, t_args, (int64_t)t_tile);
+    step_tile<BLOCK, RM, RtModel<Z>>(t_model, t_args, (int64_t)t_tile);
 }
 
 template <int BLOCK, int RM, bool Z>

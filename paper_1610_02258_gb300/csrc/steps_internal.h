@@ -8,91 +8,13 @@
 #include <vector_types.h>
 
 #include "../../include/steps_gpu.h"
+#include "steps_device.h"
 
 namespace steps {
 
-constexpr int kMaxSpecies = STEPS_MAX_SPECIES;
-constexpr int kMaxReac = STEPS_MAX_REACTIONS;
-constexpr int kMaxChanges = 6;
-constexpr double kAvogadro = 6.02214076e23;
-// Reaction events one tet may fire in one window before the kernel gives up
-// on it and raises error bit 2 (a guard against runaway rate constants).
-constexpr uint32_t kMaxEventsPerWindow = 1u << 24;
-// Full windows counted and enqueued per batch by steps_run.
-constexpr int64_t kWindowBatch = 1 << 16;
-
-// Stream purposes of the counter-based generator (top 4 bits of counter word 3).
-constexpr uint32_t kPurposeReac = 1;
-constexpr uint32_t kPurposeRound = 2;
-constexpr uint32_t kPurposeDiff = 3;
-
-// Reaction kinds by propensity form.
-enum ReacType : int8_t { kOrder0 = 0, kOrder1 = 1, kOrder2 = 2, kDimer = 3 };
+static_assert(kMaxSpecies == STEPS_MAX_SPECIES && kMaxReac == STEPS_MAX_REACTIONS, "limits");
 
 void set_error(const std::string &msg);
-
-// ---------------------------------------------------------------- device-side model
-// Propensity a = ((c x) y) in float with x = count of species ia, y = count
-// of species ib minus sub; row S of the kernel's count tile holds 1, so a
-// missing reactant reads 1. c = k (order 1), k / (N_A V) (order 2 and dimer:
-// y = n - 1) or k N_A V (order 0), the last two computed per tet.
-struct ReacDesc {
-    float k;                      // rate constant, float
-    uint32_t need;                // bit s set when species s is a reactant (a_r = 0 unless all are present)
-    int32_t ia, ib;               // count rows read for x and y (S = the row of ones)
-    int32_t sub;                  // subtracted from y: 1 for a dimer, else 0
-    int32_t type;                 // ReacType
-    int32_t nchg;                 // species changed (delta != 0), increasing species order
-    int8_t chg_s[kMaxChanges];
-    int8_t chg_d[kMaxChanges];
-};
-
-struct ModelDev {
-    int32_t S, R;
-    uint32_t diffusive;           // bit s set when D_s > 0
-    uint32_t order0;              // bit r set when reaction r has order 0
-    ReacDesc reac[kMaxReac];
-};
-
-// Arguments of one diffusion window.
-struct StepArgs {
-    int32_t *cur;                 // [S][Tpad] counts at window start; non-zero entries are zeroed as read
-    int32_t *nxt;                 // [S][Tpad] counts at window end (all entries must be zero on entry)
-    const int4 *nbr;              // [T] face neighbours (device index), -1 = boundary
-    const uint4 *thr;             // [T] cumulative face thresholds at the full window, 2^31 fixed point
-    const float *inv_nav;         // [T] 1 / (N_A V_L) as float
-    const int32_t *orig;          // [T] original tet id (RNG key), or nullptr for identity
-    const uint32_t *rmask;        // [T] active-reaction bits, or nullptr = all active
-    uint32_t *err;                // device error word
-    int32_t T, Tpad;
-    uint32_t key0, key1;          // Philox key = seed
-    uint64_t window;              // window index of this launch (RNG counter)
-    const uint64_t *window_base;  // if set, window = *window_base + window (graph replay)
-    double tau_k, inv_tau_k;
-    float tau_dn;                 // largest float <= tau_k
-    int32_t occ;                  // STEPS_OCC_*
-    int32_t prefetch;             // tiles ahead whose tables a block prefetches into L2 (0 = none)
-    uint32_t scale[kMaxSpecies];  // per-species fixed-point scale for this window length
-};
-
-// One member of a batched launch, resident in device memory. The step kernel
-// reads its member's model and arguments from here (cur/nxt chosen by
-// `parity`); the advance kernel moves `args.window` and `parity` after every
-// window while args.window < window_end.
-struct RepEntry {
-    ModelDev model;
-    StepArgs args;
-    int32_t *cnt[2];
-    uint32_t parity;
-    uint32_t pad_;
-    uint64_t window_end;
-};
-
-// A block of a batched launch: member index and tile (BLOCK consecutive tets) within it.
-struct BlockWork {
-    int32_t rep;
-    int32_t tile;
-};
 
 // ---------------------------------------------------------------- host objects
 struct HostMesh {
@@ -130,6 +52,9 @@ void build_tables(const HostMesh &mesh, const HostModel &model, int reorder, Tab
 uint32_t species_scale(const HostModel &model, const Tables &t, int s, double tau_k);
 
 // steps_kernels.cu
+// Blocks of a kernel resident on the whole GPU at once (SMs x blocks per SM),
+// cached per kernel and shared-memory size; the L2 prefetch distance.
+int resident_blocks(const void *kernel, int block, size_t smem);
 int launch_step(const ModelDev &m, const StepArgs &a, int block, void *stream);
 int launch_philox_test(uint64_t seed, const uint32_t *d_ctr, int64_t n, uint32_t *d_out, void *stream);
 int launch_logf_test(const float *d_x, int64_t n, float *d_out, void *stream);
@@ -137,5 +62,11 @@ int launch_add_u64(uint64_t *p, uint64_t v, void *stream);
 int launch_step_batch(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R,
                       bool any_order0, int block, void *stream);
 int launch_advance(RepEntry *reps, int32_t n, void *stream);
+
+// steps_spec.cpp: the step kernel specialised for one model by the run-time
+// compiler; nullptr (with the reason in *why) when it cannot be built.
+void *spec_kernel(const HostModel &hm, int block, std::string *why);
+int launch_spec(void *kernel, const ModelDev &m, const StepArgs &a, int block, void *stream);
+std::string spec_program_source(const HostModel &hm, int block);
 
 }  // namespace steps

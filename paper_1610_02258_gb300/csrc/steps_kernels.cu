@@ -11,7 +11,7 @@ namespace {
 template <int BLOCK, int RM, bool Z>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2)
     step_kernel(const __grid_constant__ ModelDev m, const __grid_constant__ StepArgs a) {
-    step_tile<BLOCK, RM, Z>(m, a, (int64_t)blockIdx.x);
+    step_tile<BLOCK, RM, RtModel<Z>>(m, a, (int64_t)blockIdx.x);
 }
 
 __global__ void philox_test_kernel(uint32_t k0, uint32_t k1, const uint4 *ctr, int64_t n, uint4 *out) {
@@ -76,6 +76,26 @@ int launch_step_b(const ModelDev &m, const StepArgs &a, void *stream) {
 }
 
 }  // namespace
+
+int resident_blocks(const void *kernel, int block, size_t smem) {
+    struct Entry {
+        const void *k;
+        size_t smem;
+        int n;
+    };
+    static thread_local Entry cache[8] = {};
+    for (const Entry &e : cache)
+        if (e.k == kernel && e.smem == smem) return e.n;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+    const int n = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    static thread_local int next = 0;
+    cache[next] = Entry{kernel, smem, n};
+    next = (next + 1) & 7;
+    return n;
+}
 
 int launch_step(const ModelDev &m, const StepArgs &a, int block, void *stream) {
     if (a.T <= 0) return STEPS_OK;

@@ -9,12 +9,13 @@
 // on a host give the same bits.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 
-#include <cstdint>
-#include <cstring>
-
 #include "steps_internal.h"
+#else
+#include "steps_device.h"
+#endif
 
 namespace steps {
 namespace {
@@ -170,16 +171,46 @@ __device__ __forceinline__ float propensity(const float4 q, const int32_t *cnt, 
     return __fmul_rn(__fmul_rn(c, __int2float_rn(x)), __int2float_rn(y));
 }
 
+// Model access of the step body. RtModel reads a model given at run time
+// (kernel parameters and the tile's reaction table). A model compiled into a
+// kernel at run time (steps_spec.cpp) provides the same functions with the
+// species, reactants and stoichiometry as constants; both read the rate
+// constants from the kernel parameters. Z: the model has order-0 reactions.
+template <bool Z>
+struct RtModel {
+    __device__ static int S(const ModelDev &m) { return m.S; }
+    __device__ static int R(const ModelDev &m) { return m.R; }
+    __device__ static uint32_t diffusive(const ModelDev &m) { return m.diffusive; }
+    __device__ static uint32_t need(const RxnTab &tb, int r) { return tb.need[r]; }
+    template <int BLOCK>
+    __device__ static void build(const ModelDev &m, RxnTab &tb) {
+        build_rxn_tab<BLOCK>(m, tb);
+    }
+    __device__ static float prop(const RxnTab &tb, const ModelDev &, int r, const int32_t *cnt, float inv_nav) {
+        return propensity(tb.p[r], cnt, inv_nav, Z);
+    }
+    // f(species, delta) for each species reaction r changes, in species order
+    template <class F>
+    __device__ static void for_changes(const RxnTab &tb, int r, F f) {
+        const uint4 c = tb.chg[r];
+        const int n = tb.nchg[r];
+        for (int q = 0; q < n; ++q) {
+            const uint32_t sw = q < 4 ? c.x : c.y, dw = q < 4 ? c.z : c.w;
+            f((int)((sw >> (8 * (q & 3))) & 0xFFu), (int)(int8_t)((dw >> (8 * (q & 3))) & 0xFFu));
+        }
+    }
+};
+
 // Running sums of the propensities in reaction order, psum[r] = a_0 + ... + a_r
 // (inactive reactions contribute 0); returns a_0 + ... + a_{R-1}.
-template <int RM>
-__device__ __forceinline__ float propensity_sums(const RxnTab &tb, int R, const int32_t *cnt, float inv_nav,
-                                                 uint32_t active, bool has_order0, float *psum) {
+template <class P, int RM>
+__device__ __forceinline__ float propensity_sums(const RxnTab &tb, const ModelDev &m, const int32_t *cnt,
+                                                 float inv_nav, uint32_t active, float *psum) {
     float a0 = 0.0f;
 #pragma unroll
     for (int r = 0; r < RM; ++r) {
-        if (r < R) {
-            const float ar = ((active >> r) & 1u) ? propensity(tb.p[r], cnt, inv_nav, has_order0) : 0.0f;
+        if (r < P::R(m)) {
+            const float ar = ((active >> r) & 1u) ? P::prop(tb, m, r, cnt, inv_nav) : 0.0f;
             a0 = __fadd_rn(a0, ar);
             psum[r] = a0;
         }
@@ -189,38 +220,27 @@ __device__ __forceinline__ float propensity_sums(const RxnTab &tb, int R, const 
 
 // The last reaction with a positive propensity (the pick when u2 a0 reaches
 // every running sum), or -1.
-__device__ __noinline__ int last_positive(const RxnTab &tb, int R, const int32_t *cnt, float inv_nav,
-                                          uint32_t active, bool has_order0) {
+template <class P, int RM>
+__device__ __noinline__ int last_positive(const RxnTab &tb, const ModelDev &m, const int32_t *cnt, float inv_nav,
+                                          uint32_t active) {
     int last = -1;
-    for (int r = 0; r < R; ++r)
-        if (((active >> r) & 1u) && propensity(tb.p[r], cnt, inv_nav, has_order0) > 0.0f) last = r;
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+        if (r < P::R(m) && ((active >> r) & 1u) && P::prop(tb, m, r, cnt, inv_nav) > 0.0f) last = r;
     return last;
 }
 
 // The reaction an event fires: the first r whose running sum exceeds
 // target = u2 a0 (running sums only grow, so that is the number of sums
 // <= target); if none does, the last reaction with a positive propensity.
-template <int RM>
-__device__ __forceinline__ int pick_reaction(const RxnTab &tb, int R, const float *psum, float target,
-                                             const int32_t *cnt, float inv_nav, uint32_t active, bool has_order0) {
+template <class P, int RM>
+__device__ __forceinline__ int pick_reaction(const RxnTab &tb, const ModelDev &m, const float *psum, float target,
+                                             const int32_t *cnt, float inv_nav, uint32_t active) {
     int n = 0;
 #pragma unroll
     for (int r = 0; r < RM; ++r)
-        if (r < R) n += psum[r] <= target ? 1 : 0;
-    return n < R ? n : last_positive(tb, R, cnt, inv_nav, active, has_order0);
-}
-
-// Applies reaction r's changes to the tet's counts (column cnt, rows BLOCK apart).
-template <int BLOCK>
-__device__ __forceinline__ void apply_changes(const RxnTab &tb, int r, int32_t *cnt) {
-    const uint4 c = tb.chg[r];
-    const int n = tb.nchg[r];
-    for (int q = 0; q < n; ++q) {
-        const uint32_t sw = q < 4 ? c.x : c.y, dw = q < 4 ? c.z : c.w;
-        const int s = (int)((sw >> (8 * (q & 3))) & 0xFFu);
-        const int d = (int)(int8_t)((dw >> (8 * (q & 3))) & 0xFFu);
-        cnt[s * BLOCK] += d;
-    }
+        if (r < P::R(m)) n += psum[r] <= target ? 1 : 0;
+    return n < P::R(m) ? n : last_positive<P, RM>(tb, m, cnt, inv_nav, active);
 }
 
 // Stochastic rounding of a mean occupancy: floor(nbar) + [u < nbar - floor(nbar)]
@@ -260,27 +280,19 @@ __device__ __forceinline__ long long round_trials(double nbar, uint32_t w) {
 // species a fired reaction changed, with its occupancy integral up to its
 // last change in O[s] and the time of that change in tS[s]. Returns error
 // bits.
-template <int BLOCK, int RM, bool Z>
+template <int BLOCK, int RM, class P>
 __device__ uint32_t ssa_tet(const RxnTab &tb, const ModelDev &m, const StepArgs &a, int32_t *cnt, uint32_t tet,
                             uint32_t c0, uint32_t c3, float inv_nav, uint32_t active, int pick0, float dt0, double *O,
                             double *tS, uint32_t &touched) {
     uint32_t bad = 0;
     touched = 0;
-    constexpr bool has0 = Z;
     double dt_acc = (double)dt0;  // 0 + (double)dt0: exact
-    {
-        // occupancy after the first event: O_S = n_before * dt0 (0 + n (dt - 0), both steps exact)
-        const uint4 c = tb.chg[pick0];
-        const int n = tb.nchg[pick0];
-        for (int q = 0; q < n; ++q) {
-            const uint32_t sw = q < 4 ? c.x : c.y, dw = q < 4 ? c.z : c.w;
-            const int s = (int)((sw >> (8 * (q & 3))) & 0xFFu);
-            const int d = (int)(int8_t)((dw >> (8 * (q & 3))) & 0xFFu);
-            O[s] = __dmul_rn((double)(cnt[s * BLOCK] - d), dt_acc);
-            tS[s] = dt_acc;
-            touched |= 1u << s;
-        }
-    }
+    // occupancy after the first event: O_S = n_before * dt0 (0 + n (dt - 0), both steps exact)
+    P::for_changes(tb, pick0, [&](int s, int d) {
+        O[s] = __dmul_rn((double)(cnt[s * BLOCK] - d), dt_acc);
+        tS[s] = dt_acc;
+        touched |= 1u << s;
+    });
     uint32_t j = 1;
     for (;;) {
         // keep the reaction table out of registers across iterations
@@ -290,7 +302,7 @@ __device__ uint32_t ssa_tet(const RxnTab &tb, const ModelDev &m, const StepArgs 
         const float neg_log_u1 = -steps_logf(unit24f(w.x));
         const float u2 = unit24f(w.y);
         float psum[RM];
-        const float a0 = propensity_sums<RM>(tb, m.R, cnt, inv_nav, active, has0, psum);
+        const float a0 = propensity_sums<P, RM>(tb, m, cnt, inv_nav, active, psum);
         if (!(a0 > 0.0f)) break;
         if (j >= kMaxEventsPerWindow) {  // pathological rates: stop and report, never spin
             bad |= 2u;
@@ -300,15 +312,10 @@ __device__ uint32_t ssa_tet(const RxnTab &tb, const ModelDev &m, const StepArgs 
         const double dt_new = __dadd_rn(dt_acc, (double)dt);
         if (dt_new > a.tau_k) break;
         ++j;
-        const int pick = pick_reaction<RM>(tb, m.R, psum, __fmul_rn(u2, a0), cnt, inv_nav, active, has0);
+        const int pick = pick_reaction<P, RM>(tb, m, psum, __fmul_rn(u2, a0), cnt, inv_nav, active);
         if (pick < 0) break;
         dt_acc = dt_new;
-        const uint4 c = tb.chg[pick];
-        const int n = tb.nchg[pick];
-        for (int q = 0; q < n; ++q) {
-            const uint32_t sw = q < 4 ? c.x : c.y, dw = q < 4 ? c.z : c.w;
-            const int s = (int)((sw >> (8 * (q & 3))) & 0xFFu);
-            const int d = (int)(int8_t)((dw >> (8 * (q & 3))) & 0xFFu);
+        P::for_changes(tb, pick, [&](int s, int d) {
             const int32_t nn = cnt[s * BLOCK];
             if ((touched >> s) & 1u) {
                 O[s] = __dadd_rn(O[s], __dmul_rn((double)nn, __dsub_rn(dt_acc, tS[s])));
@@ -318,7 +325,7 @@ __device__ uint32_t ssa_tet(const RxnTab &tb, const ModelDev &m, const StepArgs 
             tS[s] = dt_acc;
             touched |= 1u << s;
             cnt[s * BLOCK] = nn + d;
-        }
+        });
     }
     return bad;
 }
@@ -447,7 +454,7 @@ __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork 
 // mobile one by an atomic add beside the movers from the neighbours. `may`
 // holds the species that can be non-zero (non-zero at the start or changed by
 // a reaction).
-template <int BLOCK>
+template <int BLOCK, class P>
 __device__ __forceinline__ void apply_remaining(const ModelDev &m, const StepArgs &a, const int32_t *cnt_all, int t,
                                                 uint32_t may, int64_t i0) {
     int32_t *out = a.nxt + i0 + t;
@@ -457,33 +464,12 @@ __device__ __forceinline__ void apply_remaining(const ModelDev &m, const StepArg
         may &= may - 1;
         const int32_t N = cnt_all[s * BLOCK + t];
         if (N) {
-            if ((m.diffusive >> s) & 1u) atomicAdd(out + s * Tpad, N);
+            if ((P::diffusive(m) >> s) & 1u) atomicAdd(out + s * Tpad, N);
             else out[s * Tpad] = N;
         }
     }
 }
 
-// Blocks of a kernel resident on the whole GPU at once (SMs x blocks per SM),
-// cached per kernel and shared-memory size.
-__host__ inline int resident_blocks(const void *kernel, int block, size_t smem) {
-    struct Entry {
-        const void *k;
-        size_t smem;
-        int n;
-    };
-    static thread_local Entry cache[8] = {};
-    for (const Entry &e : cache)
-        if (e.k == kernel && e.smem == smem) return e.n;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
-    const int n = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    static thread_local int next = 0;
-    cache[next] = Entry{kernel, smem, n};
-    next = (next + 1) & 7;
-    return n;
-}
 
 // One diffusion window for BLOCK consecutive tets (device order).
 //  load   counts and tables into shared memory by bulk copies; each thread
@@ -503,7 +489,7 @@ __host__ inline int resident_blocks(const void *kernel, int block, size_t smem) 
 //         over the whole block, after a barrier, for chunks with reacting
 //         tets; then each tet's remaining counts are added to its own entry
 //         of `nxt`. Z: the model has order-0 reactions.
-template <int BLOCK, int RM, bool Z>
+template <int BLOCK, int RM, class P>
 __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, const int64_t tile) {
     extern __shared__ __align__(16) int32_t smem[];  // cnt [S + 1][BLOCK], trial [S][BLOCK]
     __shared__ __align__(16) uint4 s_thr[BLOCK];
@@ -522,7 +508,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     __shared__ uint32_t s_scale[kMaxSpecies];
     __shared__ __align__(8) uint64_t bar;
 
-    const int S = m.S;
+    const int S = P::S(m);
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int64_t i0 = tile * BLOCK;
@@ -545,7 +531,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         next_chunk = 0;
         mbar_init(&bar, 1);
     }
-    build_rxn_tab<BLOCK>(m, tb);
+    P::template build<BLOCK>(m, tb);
     if (tid < S) s_scale[tid] = a.scale[tid];
     __syncthreads();
     if (tid == 0) {
@@ -612,10 +598,9 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
 
     // ---- A: the tet's first reaction event, if it falls inside the window
     bool reacting = false;
-    if (m.R > 0) {
+    if (P::R(m) > 0) {
         const float inv_nav = s_inv_nav[tid];
         const uint32_t active = live ? s_mask[tid] : 0u;
-        constexpr bool has0 = Z;
         int32_t *cnt = cnt_all + tid;
         float psum[RM];
         float a0 = 0.0f;
@@ -624,16 +609,16 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         // lane r decides whether reaction r can fire in any tet of the warp
         const uint32_t wnz = __reduce_or_sync(0xFFFFFFFFu, nz);
         const uint32_t wact = __reduce_or_sync(0xFFFFFFFFu, active);
-        const uint32_t need_l = lane < m.R ? tb.need[lane] : 0u;
+        const uint32_t need_l = lane < P::R(m) ? P::need(tb, lane) : 0u;
         const uint32_t possible =
-            __ballot_sync(0xFFFFFFFFu, lane < m.R && ((wact >> lane) & 1u) && (wnz & need_l) == need_l);
+            __ballot_sync(0xFFFFFFFFu, lane < P::R(m) && ((wact >> lane) & 1u) && (wnz & need_l) == need_l);
         if (possible) {
 #pragma unroll
             for (int r = 0; r < RM; ++r) {
-                if (r < m.R) {
+                if (r < P::R(m)) {
                     float ar = 0.0f;
                     if ((possible >> r) & 1u)
-                        ar = ((active >> r) & 1u) ? propensity(tb.p[r], cnt, inv_nav, has0) : 0.0f;
+                        ar = ((active >> r) & 1u) ? P::prop(tb, m, r, cnt, inv_nav) : 0.0f;
                     a0 = __fadd_rn(a0, ar);
                     psum[r] = a0;
                 }
@@ -644,10 +629,10 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
             const float dt = __fdiv_rn(-steps_logf(unit24f(w.x)), a0);
             // 0 + (double)dt is exact, and (double)dt > tau_k <=> dt > tau_dn
             if (!(dt > a.tau_dn)) {
-                const int pick = pick_reaction<RM>(tb, m.R, psum, __fmul_rn(unit24f(w.y), a0), cnt, inv_nav,
-                                                   active, has0);
+                const int pick = pick_reaction<P, RM>(tb, m, psum, __fmul_rn(unit24f(w.y), a0), cnt, inv_nav,
+                                                      active);
                 if (pick >= 0) {
-                    apply_changes<BLOCK>(tb, pick, cnt);
+                    P::for_changes(tb, pick, [&](int s, int d) { cnt[s * BLOCK] += d; });
                     q_pick[tid] = (int8_t)pick;
                     q_dt[tid] = dt;
                     reacting = true;
@@ -694,14 +679,14 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         uint32_t touched = 0;
         double O[kMaxSpecies], tS[kMaxSpecies];
         if (reacts)
-            bad |= ssa_tet<BLOCK, RM, Z>(tb, m, a, cnt_all + t, s_tet[t], c0, c3, s_inv_nav[t], s_mask[t],
+            bad |= ssa_tet<BLOCK, RM, P>(tb, m, a, cnt_all + t, s_tet[t], c0, c3, s_inv_nav[t], s_mask[t],
                                          q_pick[t], q_dt[t], O, tS, touched);
 
         // trial counts: species that may hold molecules (non-zero at the start, or
         // changed by a reaction), diffusive, with a non-zero leave threshold
         uint32_t W = 0, hm = 0;
         if (valid) {
-            uint32_t walk = (s_nz[t] | touched) & m.diffusive;
+            uint32_t walk = (s_nz[t] | touched) & P::diffusive(m);
             const uint32_t Aw = s_thr[t].w;
             if (!touched || !a.occ) {
                 // no occupancy rounding: the trial count is the count
@@ -767,7 +752,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         for (uint32_t item = lane; item < total; item += 32)
             diffuse_block<BLOCK>(a, ww, item, trial_all, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3);
         __syncwarp();
-        if (valid) apply_remaining<BLOCK>(m, a, cnt_all, t, s_nz[t] | touched, i0);
+        if (valid) apply_remaining<BLOCK, P>(m, a, cnt_all, t, s_nz[t] | touched, i0);
         __syncwarp();
     }
 
@@ -784,7 +769,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         __syncthreads();
         for (int c = tid >> 5; c < rchunks; c += BLOCK / 32) {
             const int t = wwork[c].tet[lane];
-            if (t >= 0) apply_remaining<BLOCK>(m, a, cnt_all, t, s_nz[t] | wwork[c].touched[lane], i0);
+            if (t >= 0) apply_remaining<BLOCK, P>(m, a, cnt_all, t, s_nz[t] | wwork[c].touched[lane], i0);
         }
     }
     if (bad) atomicOr(a.err, bad);

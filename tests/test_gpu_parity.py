@@ -104,11 +104,56 @@ def test_irregular_mesh_bit_exact_many_tiles_ragged_tail(capi, occ):
 
 def test_full_size_config2_whole_run_bit_exact(capi):
     """The benchmark workload at full size (294,780 tets, 20 ms, 99 windows),
-    default launch configuration (Morton order, CUDA graph, 256 threads)."""
+    default launch configuration (Morton order, CUDA graph, 256 threads, the
+    step kernel compiled for the model)."""
     w = I.config2()
     gc, oc, g, o = run_both(capi, w.verts, w.tets, w.model, w.counts, w.seed, w.t_end)
+    assert g.specialized
     assert g.windows == 99
     assert np.array_equal(gc, oc)
+
+
+@pytest.mark.parametrize("which", ["cuboid", "box", "dendrite"])
+def test_specialised_kernel_bit_exact(capi, which):
+    """The step kernel compiled at run time for the model (forced on small
+    meshes) against the oracle: A + B <-> C; the 10-species / 20-reaction
+    network; the calcium network with a masked zero-order influx (the order-0
+    and dimer-free forms) and immobile species."""
+    if which == "cuboid":
+        w, masks = I.config1(), {}
+    elif which == "box":
+        w = I.config2(nx=6, t_end=3e-3)
+        masks = {}
+    else:
+        w = I.config3(h=0.5e-6, t_end=0.2e-3)
+        masks = w.reac_masks
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, w.model, w.counts, w.seed, w.t_end, masks=masks, specialize=1)
+    assert g.specialized
+    assert o.events > 0
+    assert np.array_equal(gc, oc)
+
+
+def test_specialised_and_generic_kernels_agree(capi):
+    """Same simulation on both kernels, several block sizes: the same bits.
+    Includes a dimer (2A -> B) and a rate change between runs."""
+    w = I.config2(nx=5, t_end=2e-3)
+    names, S = w.model.names, w.model.n_species
+    rx = [([names[s] for s in range(S) for _ in range(int(w.model.lhs[r, s]))],
+           [names[s] for s in range(S) for _ in range(int(w.model.rhs[r, s]))], float(w.model.k[r]))
+          for r in range(12)]
+    m = I.model_from_lists(names, w.model.diff, [([names[0], names[0]], [names[1]], 3e7)] + rx)
+    ref = None
+    for kw in [dict(specialize=-1), dict(specialize=1), dict(specialize=1, block=128), dict(specialize=1, block=512)]:
+        g = capi.Simulation(w.verts, w.tets, m, 11, **kw)
+        assert g.specialized == (kw["specialize"] == 1)
+        g.set_counts(w.counts)
+        g.run(w.t_end / 2)
+        g.set_reac_rate(0, 1e8)
+        g.run(w.t_end)
+        c = g.get_counts()
+        if ref is None:
+            ref = c
+        assert np.array_equal(c, ref), kw
 
 
 def test_full_size_dendrite_bit_exact(capi):
@@ -120,6 +165,7 @@ def test_full_size_dendrite_bit_exact(capi):
     g = capi.from_workload(w)
     t_end = 20.5 * g.tau
     gc, oc, g2, o = run_both(capi, w.verts, w.tets, w.model, w.counts, w.seed, t_end, masks=w.reac_masks)
+    assert g2.specialized
     assert g2.windows == 21
     assert o.events > 0
     assert np.array_equal(gc, oc)
