@@ -108,7 +108,8 @@ class Clocks:
 
 
 KERNEL_SOURCES = ["paper_1610_02258_gb300/csrc/steps_step.cuh", "paper_1610_02258_gb300/csrc/steps_kernels.cu",
-                  "paper_1610_02258_gb300/csrc/steps_batch.cu", "paper_1610_02258_gb300/csrc/steps_internal.h"]
+                  "paper_1610_02258_gb300/csrc/steps_batch.cu", "paper_1610_02258_gb300/csrc/steps_internal.h",
+                  "paper_1610_02258_gb300/csrc/steps_device.h", "paper_1610_02258_gb300/csrc/steps_spec.cpp"]
 
 
 def kernel_sources_hash() -> str:
@@ -270,7 +271,7 @@ def measure_dendrite(args, capi, I, torch, peak):
     achieved = w.n_tets * bytes_per_tet / kernel_s / 1e9
     tr = profile_traffic("step_kernel_dendrite")
     out = {"value": w.n_tets * windows / (ms / 1e3), "unit": UNIT, "workload": w.name, "tets": w.n_tets,
-           "form": "plain",
+           "form": "plain", "kernel": "specialised" if sim.specialized else "generic",
            "species": S, "reactions": w.model.n_reac, "tau_us": sim.tau * 1e6, "sim_ms_per_step": args.dendrite_ms,
            "windows_per_step": windows / steps, "ms_per_step": ms / steps, "steps": steps,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -472,6 +473,7 @@ def run_ours(args):
         "config": {"workload": w.name, "tets": w.n_tets, "species": S, "reactions": w.model.n_reac,
                    "tau_ms": tau * 1e3, "sim_ms_per_step": t_step * 1e3,
                    "windows_per_step": windows / args.steps, "form": "plain",
+                   "kernel": "specialised" if sim.specialized else "generic",
                    "l2": "flushed before each timed step (256 MiB write, outside the events)",
                    "parallelism": f"replicas{world}"},
         "e2e": e2e,
