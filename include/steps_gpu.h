@@ -211,7 +211,12 @@ typedef struct steps_batch steps_batch;
 typedef struct steps_batch_options {
     int32_t block;       /* threads per block; 0 = autotune over 128/256/512 on the first run (default) */
     int32_t use_graph;   /* 1 = replay windows from a captured CUDA graph (default) */
-    int32_t reserved[6]; /* set to 0 */
+    int32_t specialize;  /* batched kernel compiled at run time for the members' model: 0 = when all members
+                            share one model structure (species, reactions, stoichiometry, diffusive set; rates
+                            may differ), they hold at least 65,536 tets together and NVRTC is available
+                            (default), 1 = always (creation fails with STEPS_ERR_ARG if the members differ in
+                            structure, the first run with STEPS_ERR_CUDA if it cannot be built), -1 = never */
+    int32_t reserved[5]; /* set to 0 */
 } steps_batch_options;
 
 void steps_batch_options_default(steps_batch_options *opt);
@@ -246,6 +251,9 @@ int steps_batch_run(steps_batch *batch, const double *t_end);
 /* Block size in use, kernel launches issued so far, and the autotuner's
  * milliseconds per window for blocks 128/256/512 (tune_ms[3], zeros if not run). */
 int steps_batch_info(const steps_batch *batch, int32_t *block, uint64_t *launches, float *tune_ms);
+
+/* *specialized = 1 when the batch runs the model-specialised batched kernel. */
+int steps_batch_specialized(const steps_batch *batch, int32_t *specialized);
 
 /*
  * Advance `sim` to t_end on counts held in a caller-owned device buffer,

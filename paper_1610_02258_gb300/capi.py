@@ -31,7 +31,7 @@ EXPORTS = [
     "steps_last_error", "steps_debug_philox", "steps_debug_logf", "steps_run_noalloc",
     "steps_batch_options_default", "steps_batch_create", "steps_batch_destroy", "steps_batch_run",
     "steps_batch_info", "steps_sim_clone", "steps_sim_device_bytes", "steps_set_reac_rate", "steps_run_record",
-    "steps_sim_specialized",
+    "steps_sim_specialized", "steps_batch_specialized",
 ]
 
 
@@ -47,7 +47,8 @@ class steps_options(ctypes.Structure):
 
 
 class steps_batch_options(ctypes.Structure):
-    _fields_ = [("block", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("block", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("specialize", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 def _load():
@@ -88,6 +89,7 @@ def _load():
         "steps_sim_device_bytes": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64)]),
         "steps_set_reac_rate": (ctypes.c_int, [P, i32, ctypes.c_double]),
         "steps_sim_specialized": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
+        "steps_batch_specialized": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
         "steps_run_record": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_double, i32, P, i32, P, P, i64,
                                             ctypes.POINTER(ctypes.c_int64)]),
     }
@@ -304,11 +306,12 @@ def steps_batch_info(batch):
 class Batch:
     """A batch over existing Simulation objects (kept alive by this object)."""
 
-    def __init__(self, sims, block=0, use_graph=True, cuda_stream=None):
+    def __init__(self, sims, block=0, use_graph=True, cuda_stream=None, specialize=0):
         self.sims = list(sims)
         opt = steps_batch_options_default()
         opt.block = block
         opt.use_graph = 1 if use_graph else 0
+        opt.specialize = int(specialize)
         self._h = steps_batch_create([s._sim for s in self.sims], opt, cuda_stream)
 
     def run(self, t_end):
@@ -318,6 +321,12 @@ class Batch:
     @property
     def info(self):
         return steps_batch_info(self._h)
+
+    @property
+    def specialized(self):
+        v = ctypes.c_int32(0)
+        _check(lib.steps_batch_specialized(self._h, ctypes.byref(v)))
+        return bool(v.value)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -813,6 +813,10 @@ struct steps_batch {
     };
     Work work[4];  // block sizes 64, 128, 256, 512
     uint64_t launches = 0;
+    bool use_spec = false;      // run the model-specialised batched kernel
+    bool spec_forced = false;
+    void *spec[4] = {};         // per block size, compiled on first use (before any capture)
+    std::string spec_why;
     std::vector<float> tune_ms;  // autotune timings per candidate block (ms per window)
 
     static int slot(int b) { return b == 64 ? 0 : b == 128 ? 1 : b == 512 ? 3 : 2; }
@@ -845,9 +849,24 @@ struct steps_batch {
         return STEPS_OK;
     }
 
+    // the specialised batched kernel for block size b (compiled once); on
+    // failure the generic kernel takes over unless specialisation was forced
+    int prepare_spec(int b) {
+        if (!use_spec || spec[slot(b)]) return STEPS_OK;
+        spec[slot(b)] = spec_kernel(members[0]->model, b, &spec_why);
+        if (spec[slot(b)]) return STEPS_OK;
+        if (spec_forced) {
+            set_error("steps_batch_run: the specialised batched kernel could not be built: " + spec_why);
+            return STEPS_ERR_CUDA;
+        }
+        use_spec = false;
+        return STEPS_OK;
+    }
+
     int window(int b, cudaStream_t st) {  // one batched window + advance
         Work &w = work[slot(b)];
-        int rc = launch_step_batch(w.d, w.n, d_reps, max_S, max_R, any_order0, b, st);
+        int rc = use_spec && spec[slot(b)] ? launch_spec_batch(spec[slot(b)], w.d, w.n, d_reps, max_S, b, st)
+                                           : launch_step_batch(w.d, w.n, d_reps, max_S, max_R, any_order0, b, st);
         if (!rc) rc = launch_advance(d_reps, (int32_t)members.size(), st);
         launches += 2;
         return rc;
@@ -877,6 +896,7 @@ struct steps_batch {
 
     int run_windows(int b, int64_t n) {  // n windows at block size b
         int rc = build_work(b);
+        if (!rc) rc = prepare_spec(b);
         if (rc) return rc;
         int64_t done = 0;
         if (use_graph && n >= kGraphWindows) {
@@ -946,6 +966,21 @@ int steps_batch_create(steps_sim *const *members, int32_t n, const steps_batch_o
         !cuda_ok(cudaMalloc((void **)&b->d_err, 4), "steps_batch_create: alloc") ||
         !cuda_ok(cudaMemset(b->d_err, 0, 4), "steps_batch_create: memset"))
         return STEPS_ERR_OOM;
+    // the model-specialised batched kernel: all members must share one model structure
+    bool uniform = true;
+    int64_t tets = 0;
+    const std::string src0 = spec_program_source(members[0]->model, 256);
+    for (int32_t j = 0; j < n; ++j) {
+        tets += members[j]->T;
+        if (j > 0 && uniform && spec_program_source(members[j]->model, 256) != src0) uniform = false;
+    }
+    if (o.specialize > 0 && !uniform) {
+        set_error("steps_batch_create: specialize = 1 needs members that share one model structure");
+        return STEPS_ERR_ARG;
+    }
+    constexpr int64_t kSpecializeMinTets = 65536;
+    b->spec_forced = o.specialize > 0;
+    b->use_spec = uniform && (o.specialize > 0 || (o.specialize == 0 && tets >= kSpecializeMinTets));
     int rc = b->build_work(b->block);
     if (rc) return rc;
     *out = b.release();
@@ -1101,6 +1136,13 @@ int steps_batch_run(steps_batch *b, const double *t_end) {
                            : "steps_batch_run: a negative count was seen on the device");
         return STEPS_ERR_STATE;
     }
+    return STEPS_OK;
+}
+
+int steps_batch_specialized(const steps_batch *b, int32_t *specialized) {
+    CHECK_NULL(b, "steps_batch_specialized");
+    CHECK_NULL(specialized, "steps_batch_specialized");
+    *specialized = b->use_spec ? 1 : 0;
     return STEPS_OK;
 }
 

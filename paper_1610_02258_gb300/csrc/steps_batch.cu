@@ -13,28 +13,7 @@ namespace {
 template <int BLOCK, int RM, bool Z>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2)
     step_kernel_batch(const BlockWork *__restrict__ work, const RepEntry *__restrict__ reps, int32_t prefetch) {
-    __shared__ __align__(16) ModelDev t_model;
-    __shared__ __align__(16) StepArgs t_args;
-    __shared__ int32_t t_tile;
-    const BlockWork bw = work[blockIdx.x];
-    const RepEntry *e = reps + bw.rep;
-    if (e->args.window >= e->window_end) return;  // member idle in this launch (block-uniform)
-    static_assert(sizeof(ModelDev) % 4 == 0 && sizeof(StepArgs) % 4 == 0, "word copy");
-    const uint32_t *src_m = reinterpret_cast<const uint32_t *>(&e->model);
-    uint32_t *dst_m = reinterpret_cast<uint32_t *>(&t_model);
-    for (int k = threadIdx.x; k < (int)(sizeof(ModelDev) / 4); k += BLOCK) dst_m[k] = src_m[k];
-    const uint32_t *src_a = reinterpret_cast<const uint32_t *>(&e->args);
-    uint32_t *dst_a = reinterpret_cast<uint32_t *>(&t_args);
-    for (int k = threadIdx.x; k < (int)(sizeof(StepArgs) / 4); k += BLOCK) dst_a[k] = src_a[k];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        t_args.cur = e->cnt[e->parity];
-        t_args.nxt = e->cnt[e->parity ^ 1u];
-        t_args.prefetch = prefetch;  // tiles ahead within the member
-        t_tile = bw.tile;
-    }
-    __syncthreads();
-    step_tile<BLOCK, RM, RtModel<Z>>(t_model, t_args, (int64_t)t_tile);
+    batch_tile<BLOCK, RM, RtModel<Z>>(work, reps, prefetch);
 }
 
 template <int BLOCK, int RM, bool Z>

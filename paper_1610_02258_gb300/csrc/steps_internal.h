@@ -63,10 +63,13 @@ int launch_step_batch(const BlockWork *work, int64_t nblocks, RepEntry *reps, in
                       bool any_order0, int block, void *stream);
 int launch_advance(RepEntry *reps, int32_t n, void *stream);
 
-// steps_spec.cpp: the step kernel specialised for one model by the run-time
-// compiler; nullptr (with the reason in *why) when it cannot be built.
+// steps_spec.cpp: the plain and batched step kernels specialised for one
+// model by the run-time compiler (an opaque handle, cached process-wide);
+// nullptr (with the reason in *why) when they cannot be built.
 void *spec_kernel(const HostModel &hm, int block, std::string *why);
-int launch_spec(void *kernel, const ModelDev &m, const StepArgs &a, int block, void *stream);
+int launch_spec(void *spec, const ModelDev &m, const StepArgs &a, int block, void *stream);
+int launch_spec_batch(void *spec, const BlockWork *work, int64_t nblocks, RepEntry *reps, int S, int block,
+                      void *stream);
 std::string spec_program_source(const HostModel &hm, int block);
 
 }  // namespace steps

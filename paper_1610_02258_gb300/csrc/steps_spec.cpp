@@ -136,13 +136,20 @@ std::string program_source(const HostModel &hm, int block) {
       << "steps_spec_step(const __grid_constant__ steps::ModelDev m, const __grid_constant__ steps::StepArgs a) {\n"
       << "    steps::step_tile<" << block << ", " << reaction_bucket(hm.dev.R) << ", steps::SpecModel>(m, a, "
       << "(int64_t)blockIdx.x);\n}\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << 2048 / block / 2 << ")\n"
+      << "steps_spec_batch(const steps::BlockWork *__restrict__ work, const steps::RepEntry *__restrict__ reps, "
+      << "int32_t prefetch) {\n"
+      << "    steps::batch_tile<" << block << ", " << reaction_bucket(hm.dev.R) << ", steps::SpecModel>(work, reps, "
+      << "prefetch);\n}\n";
     return o.str();
 }
 
 struct Compiled {
     cudaLibrary_t lib = nullptr;
-    cudaKernel_t kern = nullptr;
-    size_t smem_set = 0;  // dynamic shared memory the kernel was opted in to
+    cudaKernel_t kern = nullptr;        // plain step kernel
+    cudaKernel_t kern_batch = nullptr;  // batched step kernel
+    size_t smem_set = 0;                // dynamic shared memory the plain kernel was opted in to
+    size_t smem_set_batch = 0;          // and the batched one
 };
 
 std::mutex g_mu;
@@ -152,7 +159,10 @@ std::map<std::string, std::shared_ptr<Compiled>> g_cache;
 
 std::string spec_program_source(const HostModel &hm, int block) { return program_source(hm, block); }
 
-void *spec_kernel(const HostModel &hm, int block, std::string *why) {
+namespace {
+
+// Compiles (once per generated source) and loads the plain and batched kernels.
+Compiled *compiled(const HostModel &hm, int block, std::string *why) {
     Nvrtc &nv = nvrtc();
     if (!nv.handle) {
         if (why) *why = nv.why;
@@ -161,7 +171,10 @@ void *spec_kernel(const HostModel &hm, int block, std::string *why) {
     const std::string src = program_source(hm, block);
     std::lock_guard<std::mutex> lock(g_mu);
     auto it = g_cache.find(src);
-    if (it != g_cache.end()) return it->second ? (void *)it->second->kern : nullptr;
+    if (it != g_cache.end()) {
+        if (!it->second && why) *why = "an earlier build of this kernel failed";
+        return it->second.get();
+    }
     nvrtc_program prog = nullptr;
     const char *hdr_src[2] = {kSrcDeviceH, kSrcStepCuh};
     const char *hdr_name[2] = {"steps_device.h", "steps_step.cuh"};
@@ -194,34 +207,42 @@ void *spec_kernel(const HostModel &hm, int block, std::string *why) {
     }
     auto c = std::make_shared<Compiled>();
     if (cudaLibraryLoadData(&c->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
-        cudaLibraryGetKernel(&c->kern, c->lib, "steps_spec_step") != cudaSuccess) {
+        cudaLibraryGetKernel(&c->kern, c->lib, "steps_spec_step") != cudaSuccess ||
+        cudaLibraryGetKernel(&c->kern_batch, c->lib, "steps_spec_batch") != cudaSuccess) {
         cudaGetLastError();
         if (why) *why = "loading the compiled kernel failed";
         g_cache[src] = nullptr;
         return nullptr;
     }
     g_cache[src] = c;
-    return (void *)c->kern;
+    return c.get();
 }
 
-int launch_spec(void *kernel, const ModelDev &m, const StepArgs &a, int block, void *stream) {
-    if (a.T <= 0) return STEPS_OK;
-    const void *fn = kernel;
-    const size_t smem = (2 * (size_t)m.S + 1) * (size_t)block * sizeof(int32_t);
-    {
-        // opt in to more than 48 KB of dynamic shared memory once per kernel and size
-        std::lock_guard<std::mutex> lock(g_mu);
-        for (auto &kv : g_cache) {
-            if (kv.second && (void *)kv.second->kern == kernel && kv.second->smem_set < smem) {
-                if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-                    set_error("specialised step kernel shared memory: " +
-                              std::string(cudaGetErrorString(cudaGetLastError())));
-                    return STEPS_ERR_CUDA;
-                }
-                kv.second->smem_set = smem;
-            }
-        }
+// Opts a kernel in to `smem` bytes of dynamic shared memory (once per size).
+bool opt_in(const void *fn, size_t smem, size_t *done) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (*done >= smem) return true;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        set_error("specialised step kernel shared memory: " + std::string(cudaGetErrorString(cudaGetLastError())));
+        return false;
     }
+    *done = smem;
+    return true;
+}
+
+}  // namespace
+
+void *spec_kernel(const HostModel &hm, int block, std::string *why) {
+    Compiled *c = compiled(hm, block, why);
+    return c ? (void *)c : nullptr;
+}
+
+int launch_spec(void *spec, const ModelDev &m, const StepArgs &a, int block, void *stream) {
+    if (a.T <= 0) return STEPS_OK;
+    Compiled *c = static_cast<Compiled *>(spec);
+    const void *fn = (const void *)c->kern;
+    const size_t smem = (2 * (size_t)m.S + 1) * (size_t)block * sizeof(int32_t);
+    if (!opt_in(fn, smem, &c->smem_set)) return STEPS_ERR_CUDA;
     StepArgs b = a;
     if (b.prefetch) b.prefetch = resident_blocks(fn, block, smem);
     ModelDev mm = m;
@@ -230,6 +251,23 @@ int launch_spec(void *kernel, const ModelDev &m, const StepArgs &a, int block, v
     cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3((unsigned)block), args, smem, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         set_error(std::string("specialised step kernel launch: ") + cudaGetErrorString(e));
+        return STEPS_ERR_CUDA;
+    }
+    return STEPS_OK;
+}
+
+int launch_spec_batch(void *spec, const BlockWork *work, int64_t nblocks, RepEntry *reps, int S, int block,
+                      void *stream) {
+    if (nblocks <= 0) return STEPS_OK;
+    Compiled *c = static_cast<Compiled *>(spec);
+    const void *fn = (const void *)c->kern_batch;
+    const size_t smem = (2 * (size_t)S + 1) * (size_t)block * sizeof(int32_t);
+    if (!opt_in(fn, smem, &c->smem_set_batch)) return STEPS_ERR_CUDA;
+    int32_t prefetch = resident_blocks(fn, block, smem);
+    void *args[3] = {(void *)&work, (void *)&reps, (void *)&prefetch};
+    cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)nblocks), dim3((unsigned)block), args, smem, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("specialised batched step kernel launch: ") + cudaGetErrorString(e));
         return STEPS_ERR_CUDA;
     }
     return STEPS_OK;

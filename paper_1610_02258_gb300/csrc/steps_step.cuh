@@ -775,5 +775,36 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     if (bad) atomicOr(a.err, bad);
 }
 
+// One block of a batched launch: the member named by work[blockIdx.x] copies
+// its model and window arguments from the device table into shared memory
+// (cur/nxt by the member's buffer parity) and runs the tile body. A member
+// whose windows are done returns at once (block-uniform).
+template <int BLOCK, int RM, class P>
+__device__ __forceinline__ void batch_tile(const BlockWork *__restrict__ work, const RepEntry *__restrict__ reps,
+                                           int32_t prefetch) {
+    __shared__ __align__(16) ModelDev t_model;
+    __shared__ __align__(16) StepArgs t_args;
+    __shared__ int32_t t_tile;
+    const BlockWork bw = work[blockIdx.x];
+    const RepEntry *e = reps + bw.rep;
+    if (e->args.window >= e->window_end) return;
+    static_assert(sizeof(ModelDev) % 4 == 0 && sizeof(StepArgs) % 4 == 0, "word copy");
+    const uint32_t *src_m = reinterpret_cast<const uint32_t *>(&e->model);
+    uint32_t *dst_m = reinterpret_cast<uint32_t *>(&t_model);
+    for (int k = threadIdx.x; k < (int)(sizeof(ModelDev) / 4); k += BLOCK) dst_m[k] = src_m[k];
+    const uint32_t *src_a = reinterpret_cast<const uint32_t *>(&e->args);
+    uint32_t *dst_a = reinterpret_cast<uint32_t *>(&t_args);
+    for (int k = threadIdx.x; k < (int)(sizeof(StepArgs) / 4); k += BLOCK) dst_a[k] = src_a[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        t_args.cur = e->cnt[e->parity];
+        t_args.nxt = e->cnt[e->parity ^ 1u];
+        t_args.prefetch = prefetch;  // tiles ahead within the member
+        t_tile = bw.tile;
+    }
+    __syncthreads();
+    step_tile<BLOCK, RM, P>(t_model, t_args, (int64_t)t_tile);
+}
+
 }  // namespace
 }  // namespace steps

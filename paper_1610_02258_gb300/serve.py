@@ -83,12 +83,15 @@ def _new_job_sim(protos, spec):
 
 class Server:
     def __init__(self, hbm_budget: int, max_jobs: int = 64, wave_windows: int = 16, block: int = 0,
-                 cuda_stream=None):
+                 cuda_stream=None, specialize: int = -1):
         self.budget = int(hbm_budget)
         self.max_jobs = max_jobs
         self.wave_windows = wave_windows
         self.block = block
         self.stream = cuda_stream
+        # batches re-form as jobs come and go: by default the generic batched kernel, so that
+        # no run-time compilation lands between requests
+        self.specialize = specialize
         self.protos = Prototypes(cuda_stream)
         self.stats = {"waves": 0, "max_active": 0, "batch_rebuilds": 0, "launches": 0, "admit_waits": 0}
 
@@ -128,7 +131,8 @@ class Server:
                 if batch is not None:
                     self.stats["launches"] += batch.info[1]
                     batch.close()
-                batch = capi.Batch([s for _, s in active], block=self.block, cuda_stream=self.stream)
+                batch = capi.Batch([s for _, s in active], block=self.block, cuda_stream=self.stream,
+                                   specialize=self.specialize)
                 members_key = key
                 self.stats["batch_rebuilds"] += 1
             # one wave: every job by up to wave_windows windows on its own grid

@@ -68,3 +68,32 @@ def test_batch_resume_and_mixed_end_times(capi):
         s.run(w.t_end)
         assert m.windows == s.windows
         assert np.array_equal(m.get_counts(), s.get_counts())
+
+
+@pytest.mark.parametrize("block", [128, 512])
+def test_specialised_batch_equals_members_alone(capi, block):
+    """Members sharing one model structure (the box network, different sizes,
+    seeds and end times): the batched kernel compiled for the model gives every
+    member's counts bit for bit as it runs alone; so does the generic one."""
+    ws = [I.config2(seed=200 + j, nx=nx, t_end=2e-3 + 0.41e-3 * j) for j, nx in enumerate([2, 9, 4, 1, 6])]
+    alone = []
+    for w in ws:
+        s = capi.from_workload(w, specialize=-1)
+        s.run(w.t_end)
+        alone.append(s.get_counts())
+    for spec in (1, -1):
+        members = [capi.from_workload(w) for w in ws]
+        b = capi.Batch(members, block=block, specialize=spec)
+        b.run([w.t_end for w in ws])
+        assert b.specialized == (spec == 1)
+        for ref, m in zip(alone, members):
+            assert np.array_equal(m.get_counts(), ref), spec
+
+
+def test_specialised_batch_needs_one_model_structure(capi):
+    ws = _workloads()[:2] + [I.config1(seed=3)]
+    members = [capi.from_workload(w) for w in ws]
+    with pytest.raises(capi.StepsError) as e:
+        capi.Batch(members, block=256, specialize=1)
+    assert e.value.code == -1
+    assert not capi.Batch(members, block=256).specialized  # auto: generic for mixed models
