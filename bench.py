@@ -283,6 +283,40 @@ def measure_dendrite(args, capi, I, torch, peak):
     return out
 
 
+def measure_cuboid(args, capi, I, torch):
+    """Plain form on the 1,920-tet cuboid (A + B <-> C, tau = 0.74 ms): the
+    launch-bound case. One step = 100 ms of simulated time (135 windows, replayed
+    from CUDA graphs)."""
+    w = I.config1()
+    stream = torch.cuda.current_stream()
+    sim = capi.from_workload(w, cuda_stream=stream.cuda_stream)
+    t_step = 100e-3
+
+    def step():
+        sim.run(sim.time + t_step)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    w0, _ = capi.steps_get_windows(sim._sim)
+    steps = max(5, min(args.steps, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    w1, _ = capi.steps_get_windows(sim._sim)
+    windows = w1 - w0
+    out = {"value": w.n_tets * windows / (ms / 1e3), "unit": UNIT, "workload": w.name, "tets": w.n_tets,
+           "form": "plain", "kernel": "specialised" if sim.specialized else "generic",
+           "sim_ms_per_step": t_step * 1e3, "windows_per_step": windows / steps, "us_per_window": 1e3 * ms / windows,
+           "bound": "launch/latency (1,920 tets fill 8 blocks of 256)"}
+    sim.close()
+    return out
+
+
 def measure_dendrite_recording(args, capi, I, torch):
     """Dendrite with a time-varying influx and recording: the influx rate
     follows a synthetic burst train, changed every 1 ms of simulated time
@@ -488,6 +522,7 @@ def run_ours(args):
     }
     if world == 1 and not args.no_forms and args.workload == "irregular-box":
         line["forms"] = {"plain": {"value": value, "unit": UNIT, "workload": w.name},
+                         "plain_cuboid": measure_cuboid(args, capi, I, torch),
                          "plain_dendrite": measure_dendrite(args, capi, I, torch, peak) if args.dendrite_ms > 0 else None,
                          "dendrite_influx_recording": (measure_dendrite_recording(args, capi, I, torch)
                                                        if args.dendrite_ms > 0 else None),
