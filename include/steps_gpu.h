@@ -19,7 +19,8 @@
  *     until the matching *_destroy.
  *   - Tet indices are always the caller's original order (the library may
  *     reorder tets internally for locality; results do not depend on it).
- *   - Host pointers unless a name ends in _device (CUDA device pointers).
+ *   - Host pointers, except arguments whose names start with d_ (CUDA device
+ *     pointers, e.g. d_counts of steps_run_noalloc, d_out of steps_run_record).
  *   - A NULL handle or array, or a size out of range, gives STEPS_ERR_ARG.
  *   - Units: metres, seconds, m^2/s; rate constants in SI (order 0: M/s,
  *     order 1: 1/s, order 2: 1/(M s)).

@@ -27,11 +27,14 @@ def capi():
     return c
 
 
-def test_noalloc_equals_steps_run_on_two_calls_in_a_row(capi):
+@pytest.mark.parametrize("specialize", [-1, 1])
+def test_noalloc_equals_steps_run_on_two_calls_in_a_row(capi, specialize):
+    """On the generic step kernel and on the one compiled for the model."""
     import torch
     w = I.config2(nx=8, t_end=4e-3)  # 13,872 tets, 10 species, 20 reactions
-    ref = capi.from_workload(w)
-    new = capi.from_workload(w)  # same seed, tables and clock; its own buffers stay unused
+    ref = capi.from_workload(w, specialize=specialize)
+    new = capi.from_workload(w, specialize=specialize)  # same seed, tables and clock; its own buffers stay unused
+    assert new.specialized == (specialize == 1)
     d_counts = torch.from_numpy(np.ascontiguousarray(w.counts)).to("cuda")
     tau = ref.tau
     # first call ends off the window grid (a shortened window), the second on it
