@@ -53,6 +53,14 @@ __global__ void gather_to_original_order(const int32_t *src, int64_t nt, int32_t
 
 __global__ void set_u64_kernel(uint64_t *p, uint64_t v) { *p = v; }
 
+// *flag |= 1 if any of src[0..n) is negative (grid-stride; one atomic per warp at most)
+__global__ void any_negative(const int32_t *src, int64_t n, uint32_t *flag) {
+    bool neg = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        neg |= src[i] < 0;
+    if (__any_sync(0xFFFFFFFFu, neg) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
 bool cuda_ok(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return true;
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -80,7 +88,7 @@ struct steps_sim {
     int32_t *d_inv_perm = nullptr;  // original id -> device index (null without reordering)
     uint32_t *d_rmask = nullptr;
     std::vector<uint32_t> h_rmask;  // device order
-    uint32_t *d_err = nullptr;
+    uint32_t *d_err = nullptr;      // [2]: window error word, input check flag
     uint64_t *d_window_base = nullptr;
     int32_t *d_stage = nullptr;     // [S * nt] original-order staging
     int32_t *d_rec = nullptr;       // recording selection (species, then tets)
@@ -341,7 +349,7 @@ int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t 
     alloc((void **)&s->d_nbr, Tpad * 16);
     alloc((void **)&s->d_thr, Tpad * 16);
     alloc((void **)&s->d_inv_nav, Tpad * 4);
-    alloc((void **)&s->d_err, 4);
+    alloc((void **)&s->d_err, 8);
     alloc((void **)&s->d_window_base, 8);
     alloc((void **)&s->d_stage, S * T * 4);
     if (reordered) {
@@ -362,7 +370,7 @@ int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t 
                       "upload inv_nav") &&
               cuda_ok(cudaMemset(s->d_cnt[0], 0, S * Tpad * 4), "memset") &&
               cuda_ok(cudaMemset(s->d_cnt[1], 0, S * Tpad * 4), "memset") &&
-              cuda_ok(cudaMemset(s->d_err, 0, 4), "memset") && cuda_ok(cudaMemset(s->d_window_base, 0, 8), "memset");
+              cuda_ok(cudaMemset(s->d_err, 0, 8), "memset") && cuda_ok(cudaMemset(s->d_window_base, 0, 8), "memset");
     if (ok && reordered)
         ok = cuda_ok(cudaMemset(s->d_orig, 0, Tpad * 4), "memset") &&
              cuda_ok(cudaMemcpy(s->d_orig, s->tab.perm.data(), T * 4, cudaMemcpyHostToDevice), "upload perm") &&
@@ -415,7 +423,7 @@ int steps_sim_clone(const steps_sim *src, uint64_t seed, void *cuda_stream, step
     alloc((void **)&s->d_nbr, Tpad * 16);
     alloc((void **)&s->d_thr, Tpad * 16);
     alloc((void **)&s->d_inv_nav, Tpad * 4);
-    alloc((void **)&s->d_err, 4);
+    alloc((void **)&s->d_err, 8);
     alloc((void **)&s->d_window_base, 8);
     alloc((void **)&s->d_stage, S * T * 4);
     if (src->d_orig) {
@@ -434,7 +442,7 @@ int steps_sim_clone(const steps_sim *src, uint64_t seed, void *cuda_stream, step
               cuda_ok(cudaMemcpyAsync(s->d_inv_nav, src->d_inv_nav, Tpad * 4, cudaMemcpyDeviceToDevice, st), "clone") &&
               cuda_ok(cudaMemsetAsync(s->d_cnt[0], 0, S * Tpad * 4, st), "clone") &&
               cuda_ok(cudaMemsetAsync(s->d_cnt[1], 0, S * Tpad * 4, st), "clone") &&
-              cuda_ok(cudaMemsetAsync(s->d_err, 0, 4, st), "clone") &&
+              cuda_ok(cudaMemsetAsync(s->d_err, 0, 8, st), "clone") &&
               cuda_ok(cudaMemsetAsync(s->d_window_base, 0, 8, st), "clone");
     if (ok && src->d_orig)
         ok = cuda_ok(cudaMemcpyAsync(s->d_orig, src->d_orig, Tpad * 4, cudaMemcpyDeviceToDevice, st), "clone") &&
@@ -450,7 +458,7 @@ int steps_sim_device_bytes(const steps_sim *sim, int64_t *bytes) {
     CHECK_NULL(sim, "steps_sim_device_bytes");
     CHECK_NULL(bytes, "steps_sim_device_bytes");
     const int64_t Tpad = sim->Tpad, S = sim->S, T = sim->T;
-    *bytes = 2 * S * Tpad * 4 + Tpad * 16 * 2 + Tpad * 4 + 12 + S * T * 4 + (sim->d_orig ? Tpad * 4 + T * 4 : 0) +
+    *bytes = 2 * S * Tpad * 4 + Tpad * 16 * 2 + Tpad * 4 + 16 + S * T * 4 + (sim->d_orig ? Tpad * 4 + T * 4 : 0) +
              (sim->d_rmask ? Tpad * 4 : 0);
     return STEPS_OK;
 }
@@ -467,6 +475,21 @@ static int put_counts(steps_sim *sim, int32_t s0, int32_t ns, const int32_t *cou
     if (!cuda_ok(cudaMemcpyAsync(sim->d_stage, counts, (size_t)ns * T * 4, cudaMemcpyHostToDevice, sim->stream),
                  "steps_set_counts: copy"))
         return STEPS_ERR_CUDA;
+    // reject negative counts on the device, before anything of the state changes
+    uint32_t neg = 0;
+    const int64_t n = (int64_t)ns * (int64_t)T;
+    if (!cuda_ok(cudaMemsetAsync(sim->d_err + 1, 0, 4, sim->stream), "steps_set_counts: check"))
+        return STEPS_ERR_CUDA;
+    any_negative<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, sim->stream>>>(sim->d_stage, n,
+                                                                                               sim->d_err + 1);
+    if (!cuda_ok(cudaGetLastError(), "steps_set_counts: check") ||
+        !cuda_ok(cudaMemcpyAsync(&neg, sim->d_err + 1, 4, cudaMemcpyDeviceToHost, sim->stream), "steps_set_counts: check") ||
+        !cuda_ok(cudaStreamSynchronize(sim->stream), "steps_set_counts: check"))
+        return STEPS_ERR_CUDA;
+    if (neg) {
+        set_error("steps_set_counts: negative count");
+        return STEPS_ERR_ARG;
+    }
     scatter_to_device_order<<<(unsigned)((T + 255) / 256), 256, 0, sim->stream>>>(
         sim->d_stage, (int64_t)T, ns, sim->d_inv_perm, sim->d_cnt[sim->cur] + (size_t)s0 * Tpad, Tpad);
     if (!cuda_ok(cudaGetLastError(), "steps_set_counts: scatter")) return STEPS_ERR_CUDA;
@@ -479,14 +502,6 @@ static int put_counts(steps_sim *sim, int32_t s0, int32_t ns, const int32_t *cou
     return STEPS_OK;
 }
 
-static int check_counts(const int32_t *c, size_t n, const char *who) {
-    for (size_t i = 0; i < n; ++i)
-        if (c[i] < 0) {
-            set_error(std::string(who) + ": negative count");
-            return STEPS_ERR_ARG;
-        }
-    return STEPS_OK;
-}
 
 int steps_set_counts(steps_sim *sim, int32_t species, const int32_t *counts) {
     CHECK_NULL(sim, "steps_set_counts");
@@ -495,15 +510,13 @@ int steps_set_counts(steps_sim *sim, int32_t species, const int32_t *counts) {
         set_error("steps_set_counts: species out of range");
         return STEPS_ERR_ARG;
     }
-    int rc = check_counts(counts, (size_t)sim->T, "steps_set_counts");
-    return rc ? rc : put_counts(sim, species, 1, counts);
+    return put_counts(sim, species, 1, counts);
 }
 
 int steps_set_counts_all(steps_sim *sim, const int32_t *counts) {
     CHECK_NULL(sim, "steps_set_counts_all");
     CHECK_NULL(counts, "steps_set_counts_all");
-    int rc = check_counts(counts, (size_t)sim->T * sim->S, "steps_set_counts_all");
-    return rc ? rc : put_counts(sim, 0, sim->S, counts);
+    return put_counts(sim, 0, sim->S, counts);
 }
 
 static int fetch_counts(const steps_sim *sim, int32_t s0, int32_t ns, int32_t *out) {
