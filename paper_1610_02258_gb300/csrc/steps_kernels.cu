@@ -51,8 +51,20 @@ int launch_step_t(const ModelDev &m, const StepArgs &a, void *stream) {
         // about one resident wave ahead
         b.prefetch = resident_blocks(reinterpret_cast<const void *>(step_kernel<BLOCK, RM, Z>), BLOCK, smem);
     }
-    step_kernel<BLOCK, RM, Z><<<(unsigned)grid, BLOCK, smem, (cudaStream_t)stream>>>(m, b);
-    cudaError_t e = cudaGetLastError();
+    // programmatic dependent launch: overlaps this window's set-up with the
+    // previous window's tail (the kernel waits for it before reading counts)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(BLOCK);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, step_kernel<BLOCK, RM, Z>, m, b);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error(std::string("step kernel launch: ") + cudaGetErrorString(e));
         return STEPS_ERR_CUDA;

@@ -248,7 +248,18 @@ int launch_spec(void *spec, const ModelDev &m, const StepArgs &a, int block, voi
     ModelDev mm = m;
     void *args[2] = {(void *)&mm, (void *)&b};
     const unsigned grid = (unsigned)((a.T + block - 1) / block);
-    cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3((unsigned)block), args, smem, (cudaStream_t)stream);
+    // programmatic dependent launch, as the generic step kernel
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
     if (e != cudaSuccess) {
         set_error(std::string("specialised step kernel launch: ") + cudaGetErrorString(e));
         return STEPS_ERR_CUDA;

@@ -517,11 +517,15 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     const bool live = tid < nlive;
     int32_t *cnt_all = smem;                              // rows 0..S-1 counts, row S ones
     int32_t *trial_all = smem + (size_t)(S + 1) * BLOCK;
-    const uint64_t window = a.window + (a.window_base ? *a.window_base : 0ull);
-    const uint32_t c0 = (uint32_t)window;
-    const uint32_t c3 = (uint32_t)(window >> 32) & 0x0FFFFFFFu;
+    uint32_t c0, c3;  // RNG counter words of the window, set once the previous window is done
     const size_t Tpad = (size_t)a.Tpad;
     uint32_t bad = 0;
+
+    // Programmatic dependent launch: the next window's grid may start its
+    // blocks as soon as every block of this one has started; they run up to
+    // griddepcontrol.wait below (set-up and the copies of the constant tables)
+    // while this grid drains. Without such a launch both are no-ops.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     // ---- load: the block's tile of every table, by TMA bulk copies into
     // shared memory (rows padded to 16 bytes; the tables are padded to Tpad)
@@ -539,12 +543,27 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         const uint32_t bytes = (uint32_t)S * n4 * 4u + 2u * (uint32_t)nlive * 16u + n4 * 4u +
                                (a.orig ? n4 * 4u : 0u) + (a.rmask ? n4 * 4u : 0u);
         mbar_expect_tx(&bar, bytes);
-        for (int s = 0; s < S; ++s) bulk_g2s(cnt_all + s * BLOCK, a.cur + s * Tpad + i0, n4 * 4u, &bar);
+        // the tables no window writes
         bulk_g2s(s_thr, a.thr + i0, (uint32_t)nlive * 16u, &bar);
         bulk_g2s(s_nbr, a.nbr + i0, (uint32_t)nlive * 16u, &bar);
         bulk_g2s(s_inv_nav, a.inv_nav + i0, n4 * 4u, &bar);
         if (a.orig) bulk_g2s(s_tet, a.orig + i0, n4 * 4u, &bar);
         if (a.rmask) bulk_g2s(s_mask, a.rmask + i0, n4 * 4u, &bar);
+    }
+    if (!a.orig) s_tet[tid] = (uint32_t)i;
+    if (!a.rmask) s_mask[tid] = 0xFFFFFFFFu;
+    cnt_all[S * BLOCK + tid] = 1;
+    // the counts and the window index come from the previous window: wait for
+    // it to complete (and its memory to be visible)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    {
+        const uint64_t window = a.window + (a.window_base ? *a.window_base : 0ull);
+        c0 = (uint32_t)window;
+        c3 = (uint32_t)(window >> 32) & 0x0FFFFFFFu;
+    }
+    if (tid == 0) {
+        const uint32_t n4 = ((uint32_t)nlive + 3u) & ~3u;
+        for (int s = 0; s < S; ++s) bulk_g2s(cnt_all + s * BLOCK, a.cur + s * Tpad + i0, n4 * 4u, &bar);
         // the tile `prefetch` tiles ahead, processed about one resident wave
         // later, into L2
         const int64_t p0 = i0 + (int64_t)a.prefetch * BLOCK;
@@ -559,9 +578,6 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
             if (a.rmask) bulk_prefetch_l2(a.rmask + p0, p4 * 4u);
         }
     }
-    if (!a.orig) s_tet[tid] = (uint32_t)i;
-    if (!a.rmask) s_mask[tid] = 0xFFFFFFFFu;
-    cnt_all[S * BLOCK + tid] = 1;
     // one thread waits for the copies (bounded) while the others sleep at the
     // barrier; then every thread observes the completed phase itself
     bool arrived = true;
