@@ -94,6 +94,7 @@ struct steps_sim {
     int32_t *d_rec = nullptr;       // recording selection (species, then tets)
     size_t rec_bytes = 0;
     void *spec = nullptr;           // step kernel compiled for this model (cached process-wide), or null
+    int32_t *d_trial = nullptr;     // [S][Tpad] trial counts for specialised kernels that keep them in global memory
     std::string spec_why;           // why there is none
     // time
     double t_base = 0.0;
@@ -121,6 +122,16 @@ struct steps_sim {
         cudaFree(d_window_base);
         cudaFree(d_stage);
         cudaFree(d_rec);
+        cudaFree(d_trial);
+    }
+
+    // the global trial buffer the model-specialised kernels of this model need (if any)
+    int ensure_trial() {
+        if (d_trial || !spec_global_trial(model)) return STEPS_OK;
+        if (!cuda_ok(cudaMalloc((void **)&d_trial, (size_t)S * (size_t)Tpad * 4), "trial buffer"))
+            return STEPS_ERR_OOM;
+        drop_graphs();  // the captured launches hold the old arguments
+        return STEPS_OK;
     }
 
     void drop_graphs() {
@@ -153,6 +164,7 @@ struct steps_sim {
         if ((double)a.tau_dn > tau_k) a.tau_dn = std::nextafter(a.tau_dn, 0.0f);
         a.occ = opt.occupancy;
         a.prefetch = 1;  // launch_step sets the distance: one resident wave
+        a.trial = d_trial;
         std::memcpy(a.scale, scale, sizeof(a.scale));
         return a;
     }
@@ -385,6 +397,10 @@ int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t 
             set_error("steps_sim_create: the specialised step kernel could not be built: " + s->spec_why);
             return STEPS_ERR_CUDA;
         }
+        if (s->spec) {
+            int rc = s->ensure_trial();
+            if (rc) return rc;
+        }
     } else {
         s->spec_why = "not requested";
     }
@@ -431,6 +447,7 @@ int steps_sim_clone(const steps_sim *src, uint64_t seed, void *cuda_stream, step
         alloc((void **)&s->d_inv_perm, T * 4);
     }
     if (src->d_rmask) alloc((void **)&s->d_rmask, Tpad * 4);
+    if (src->d_trial) alloc((void **)&s->d_trial, S * Tpad * 4);
     if (e != cudaSuccess) {
         set_error(std::string("steps_sim_clone: device allocation failed: ") + cudaGetErrorString(e));
         cudaGetLastError();
@@ -459,6 +476,7 @@ int steps_sim_device_bytes(const steps_sim *sim, int64_t *bytes) {
     CHECK_NULL(bytes, "steps_sim_device_bytes");
     const int64_t Tpad = sim->Tpad, S = sim->S, T = sim->T;
     *bytes = 2 * S * Tpad * 4 + Tpad * 16 * 2 + Tpad * 4 + 16 + S * T * 4 + (sim->d_orig ? Tpad * 4 + T * 4 : 0) +
+             (sim->d_trial ? S * Tpad * 4 : 0) +
              (sim->d_rmask ? Tpad * 4 : 0);
     return STEPS_OK;
 }
@@ -994,6 +1012,11 @@ int steps_batch_create(steps_sim *const *members, int32_t n, const steps_batch_o
     constexpr int64_t kSpecializeMinTets = 65536;
     b->spec_forced = o.specialize > 0;
     b->use_spec = uniform && (o.specialize > 0 || (o.specialize == 0 && tets >= kSpecializeMinTets));
+    if (b->use_spec)
+        for (steps_sim *m : b->members) {
+            int rc = m->ensure_trial();
+            if (rc) return rc;
+        }
     int rc = b->build_work(b->block);
     if (rc) return rc;
     *out = b.release();

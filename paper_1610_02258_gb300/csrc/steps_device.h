@@ -80,6 +80,7 @@ struct StepArgs {
     float tau_dn;                 // largest float <= tau_k
     int32_t occ;                  // STEPS_OCC_*
     int32_t prefetch;             // tiles ahead whose tables a block prefetches into L2 (0 = none)
+    int32_t *trial;               // [S][Tpad] trial counts, for kernels that keep them in global memory
     uint32_t scale[kMaxSpecies];  // per-species fixed-point scale for this window length
 };
 

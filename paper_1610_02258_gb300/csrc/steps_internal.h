@@ -71,5 +71,7 @@ int launch_spec(void *spec, const ModelDev &m, const StepArgs &a, int block, voi
 int launch_spec_batch(void *spec, const BlockWork *work, int64_t nblocks, RepEntry *reps, int S, int block,
                       void *stream);
 std::string spec_program_source(const HostModel &hm, int block);
+// whether the specialised kernels keep the trial counts in StepArgs::trial
+bool spec_global_trial(const HostModel &hm);
 
 }  // namespace steps

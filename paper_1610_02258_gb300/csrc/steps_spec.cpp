@@ -75,6 +75,14 @@ Nvrtc &nvrtc() {
     return n;
 }
 
+}  // namespace
+
+// Models with many species keep the trial counts in a global buffer: their
+// tile's shared memory then fits four resident blocks per SM.
+bool spec_global_trial(const HostModel &hm) { return hm.dev.S >= 16; }
+
+namespace {
+
 std::string hex_u32(uint32_t v) {
     std::ostringstream o;
     o << "0x" << std::hex << v << "u";
@@ -90,6 +98,7 @@ std::string policy_source(const HostModel &hm, int block) {
     const ModelDev &m = hm.dev;
     std::ostringstream o;
     o << "namespace steps {\nnamespace {\nstruct SpecModel {\n";
+    o << "    static constexpr bool kGlobalTrial = " << (spec_global_trial(hm) ? "true" : "false") << ";\n";
     o << "    __device__ static int S(const ModelDev &) { return " << m.S << "; }\n";
     o << "    __device__ static int R(const ModelDev &) { return " << m.R << "; }\n";
     o << "    __device__ static uint32_t diffusive(const ModelDev &) { return " << hex_u32(m.diffusive) << "; }\n";
@@ -150,6 +159,7 @@ struct Compiled {
     cudaKernel_t kern_batch = nullptr;  // batched step kernel
     size_t smem_set = 0;                // dynamic shared memory the plain kernel was opted in to
     size_t smem_set_batch = 0;          // and the batched one
+    bool global_trial = false;          // trial counts in StepArgs::trial, not shared memory
 };
 
 std::mutex g_mu;
@@ -206,6 +216,7 @@ Compiled *compiled(const HostModel &hm, int block, std::string *why) {
         return nullptr;
     }
     auto c = std::make_shared<Compiled>();
+    c->global_trial = spec_global_trial(hm);
     if (cudaLibraryLoadData(&c->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
         cudaLibraryGetKernel(&c->kern, c->lib, "steps_spec_step") != cudaSuccess ||
         cudaLibraryGetKernel(&c->kern_batch, c->lib, "steps_spec_batch") != cudaSuccess) {
@@ -241,7 +252,7 @@ int launch_spec(void *spec, const ModelDev &m, const StepArgs &a, int block, voi
     if (a.T <= 0) return STEPS_OK;
     Compiled *c = static_cast<Compiled *>(spec);
     const void *fn = (const void *)c->kern;
-    const size_t smem = (2 * (size_t)m.S + 1) * (size_t)block * sizeof(int32_t);
+    const size_t smem = ((size_t)m.S + 1 + (c->global_trial ? 0 : (size_t)m.S)) * (size_t)block * sizeof(int32_t);
     if (!opt_in(fn, smem, &c->smem_set)) return STEPS_ERR_CUDA;
     StepArgs b = a;
     if (b.prefetch) b.prefetch = resident_blocks(fn, block, smem);
@@ -272,7 +283,7 @@ int launch_spec_batch(void *spec, const BlockWork *work, int64_t nblocks, RepEnt
     if (nblocks <= 0) return STEPS_OK;
     Compiled *c = static_cast<Compiled *>(spec);
     const void *fn = (const void *)c->kern_batch;
-    const size_t smem = (2 * (size_t)S + 1) * (size_t)block * sizeof(int32_t);
+    const size_t smem = ((size_t)S + 1 + (c->global_trial ? 0 : (size_t)S)) * (size_t)block * sizeof(int32_t);
     if (!opt_in(fn, smem, &c->smem_set_batch)) return STEPS_ERR_CUDA;
     int32_t prefetch = resident_blocks(fn, block, smem);
     void *args[3] = {(void *)&work, (void *)&reps, (void *)&prefetch};

@@ -178,6 +178,7 @@ __device__ __forceinline__ float propensity(const float4 q, const int32_t *cnt, 
 // constants from the kernel parameters. Z: the model has order-0 reactions.
 template <bool Z>
 struct RtModel {
+    static constexpr bool kGlobalTrial = false;  // trial counts in shared memory
     __device__ static int S(const ModelDev &m) { return m.S; }
     __device__ static int R(const ModelDev &m) { return m.R; }
     __device__ static uint32_t diffusive(const ModelDev &m) { return m.diffusive; }
@@ -382,7 +383,8 @@ struct WarpWork {
 // added to the neighbour's entry of nxt and removed from the tet's count.
 template <int BLOCK>
 __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork &ww, uint32_t item,
-                                              const int32_t *trial_all, int32_t *cnt_all, const uint4 *s_thr,
+                                              const int32_t *trial_all, size_t tstride, int32_t *cnt_all,
+                                              const uint4 *s_thr,
                                               const int4 *s_nbr, const uint32_t *s_tet, const uint32_t *s_scale,
                                               uint32_t c0, uint32_t c3) {
     int lane, s;
@@ -408,18 +410,18 @@ __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork 
         uint32_t hm = ww.hm[lane];
         s = __ffs(hm) - 1;
         before = 0;
-        uint32_t end = (uint32_t)trial_all[s * BLOCK + t];
+        uint32_t end = (uint32_t)trial_all[s * tstride + t];
         while (4u * k >= end) {
             hm &= hm - 1;
             s = __ffs(hm) - 1;
             before = end;
-            end += (uint32_t)trial_all[s * BLOCK + t];
+            end += (uint32_t)trial_all[s * tstride + t];
         }
     }
     const int t = ww.tet[lane];
     const uint32_t Wt = ww.W[lane];
     uint32_t hm = ww.hm[lane] & ~((2u << s) - 1u);  // species after s
-    uint32_t end = before + (uint32_t)trial_all[s * BLOCK + t];
+    uint32_t end = before + (uint32_t)trial_all[s * tstride + t];
     const uint4 A = s_thr[t];
     const int4 nb = s_nbr[t];
     const size_t Tpad = (size_t)a.Tpad;
@@ -433,7 +435,7 @@ __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork 
             if (w >= end) {  // next species with trial molecules
                 s = __ffs(hm) - 1;
                 hm &= hm - 1;
-                end += (uint32_t)trial_all[s * BLOCK + t];
+                end += (uint32_t)trial_all[s * tstride + t];
                 species_thresholds(A, s_scale[s], T0, T1, T2, T3);
             }
             const uint32_t x = word_of(rw, q) >> 1;
@@ -516,7 +518,12 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     const int nlive = (int)min((int64_t)BLOCK, (int64_t)a.T - i0);
     const bool live = tid < nlive;
     int32_t *cnt_all = smem;                              // rows 0..S-1 counts, row S ones
-    int32_t *trial_all = smem + (size_t)(S + 1) * BLOCK;
+    // trial counts [S][tstride]: after the count rows in shared memory, or (for
+    // models with many species, to leave room for more resident blocks) the
+    // tile's columns of a global buffer
+    constexpr bool GT = P::kGlobalTrial;
+    int32_t *trial_all = GT ? a.trial + i0 : smem + (size_t)(S + 1) * BLOCK;
+    const size_t tstride = GT ? (size_t)a.Tpad : (size_t)BLOCK;
     uint32_t c0, c3;  // RNG counter words of the window, set once the previous window is done
     const size_t Tpad = (size_t)a.Tpad;
     uint32_t bad = 0;
@@ -711,7 +718,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
                     walk &= walk - 1;
                     const int32_t M = cnt_all[s * BLOCK + t];
                     if (M > 0 && (uint32_t)(((uint64_t)Aw * s_scale[s]) >> 31) != 0u) {
-                        trial_all[s * BLOCK + t] = M;
+                        trial_all[s * tstride + t] = M;
                         hm |= 1u << s;
                         W += (uint32_t)M;
                     }
@@ -726,7 +733,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
                     const int32_t M = trial_count(a, s, cnt_all[s * BLOCK + t], (touched >> s) & 1u, O, tS,
                                                   s_tet[t], c0, c3, rblk, rb);
                     if (M > 0) {
-                        trial_all[s * BLOCK + t] = M;
+                        trial_all[s * tstride + t] = M;
                         hm |= 1u << s;
                         W += (uint32_t)M;
                     }
@@ -751,13 +758,13 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         if (lane == 31) ww.first[32] = total;
         if (nb > 0 && first < (uint32_t)kMapCap) {
             int s = __ffs(hm) - 1;
-            uint32_t h = hm & (hm - 1), before = 0, end = (uint32_t)trial_all[s * BLOCK + t];
+            uint32_t h = hm & (hm - 1), before = 0, end = (uint32_t)trial_all[s * tstride + t];
             for (uint32_t k = 0; k < nb && first + k < (uint32_t)kMapCap; ++k) {
                 while (4u * k >= end) {
                     s = __ffs(h) - 1;
                     h &= h - 1;
                     before = end;
-                    end += (uint32_t)trial_all[s * BLOCK + t];
+                    end += (uint32_t)trial_all[s * tstride + t];
                 }
                 ww.map_own[first + k] = (uint32_t)lane | ((uint32_t)s << 5) | (k << 10);
                 ww.map_before[first + k] = before;
@@ -766,7 +773,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         __syncwarp();
         if (ch < (uint32_t)rchunks) continue;  // diffusion in phase 2
         for (uint32_t item = lane; item < total; item += 32)
-            diffuse_block<BLOCK>(a, ww, item, trial_all, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3);
+            diffuse_block<BLOCK>(a, ww, item, trial_all, tstride, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3);
         __syncwarp();
         if (valid) apply_remaining<BLOCK, P>(m, a, cnt_all, t, s_nz[t] | touched, i0);
         __syncwarp();
@@ -780,7 +787,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
             const WarpWork &ww = wwork[c];
             const uint32_t total = ww.first[32];
             for (uint32_t item = tid; item < total; item += BLOCK)
-                diffuse_block<BLOCK>(a, ww, item, trial_all, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3);
+                diffuse_block<BLOCK>(a, ww, item, trial_all, tstride, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3);
         }
         __syncthreads();
         for (int c = tid >> 5; c < rchunks; c += BLOCK / 32) {
