@@ -82,15 +82,16 @@ def _new_job_sim(protos, spec):
 
 
 class Server:
-    def __init__(self, hbm_budget: int, max_jobs: int = 64, wave_windows: int = 16, block: int = 0,
+    def __init__(self, hbm_budget: int, max_jobs: int = 64, wave_windows: int = 16, block: int = 256,
                  cuda_stream=None, specialize: int = -1):
         self.budget = int(hbm_budget)
         self.max_jobs = max_jobs
         self.wave_windows = wave_windows
         self.block = block
         self.stream = cuda_stream
-        # batches re-form as jobs come and go: by default the generic batched kernel, so that
-        # no run-time compilation lands between requests
+        # batches re-form as jobs come and go: by default a fixed block size (no autotuning
+        # windows on every re-formed batch) and the generic batched kernel (no run-time
+        # compilation between requests)
         self.specialize = specialize
         self.protos = Prototypes(cuda_stream)
         self.stats = {"waves": 0, "max_active": 0, "batch_rebuilds": 0, "launches": 0, "admit_waits": 0}
