@@ -97,3 +97,23 @@ def test_specialised_batch_needs_one_model_structure(capi):
         capi.Batch(members, block=256, specialize=1)
     assert e.value.code == -1
     assert not capi.Batch(members, block=256).specialized  # auto: generic for mixed models
+
+
+def test_specialised_batch_of_many_species_models(capi):
+    """Dendrite replicates (20 species, masked influx): the specialised batched
+    kernel keeps trial counts in global memory; members created without a
+    specialised kernel of their own get the buffer from the batch. Every
+    member equals its run alone."""
+    ws = [I.config3(seed=300 + j, h=0.55e-6, t_end=0.1e-3 + 0.03e-3 * j) for j in range(3)]
+    alone = []
+    for w in ws:
+        s = capi.from_workload(w, specialize=-1)
+        s.run(w.t_end)
+        alone.append(s.get_counts())
+    members = [capi.from_workload(w, specialize=-1) for w in ws]
+    assert not any(m.specialized for m in members)
+    b = capi.Batch(members, block=256, specialize=1)
+    assert b.specialized
+    b.run([w.t_end for w in ws])
+    for ref, m in zip(alone, members):
+        assert np.array_equal(m.get_counts(), ref)
