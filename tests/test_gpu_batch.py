@@ -70,6 +70,28 @@ def test_batch_resume_and_mixed_end_times(capi):
         assert np.array_equal(m.get_counts(), s.get_counts())
 
 
+def test_plain_batched_plain_handoff(capi):
+    """A member that runs alone, then in a batch of block size 128 for an odd
+    number of windows (its count buffers swap), then alone again equals the
+    same member run alone throughout."""
+    ws = [I.config3(h=0.5e-6, t_end=0.2e-3), I.config2(seed=41, nx=4, t_end=3e-3)]
+    for spec in (-1, 1):
+        for w in ws:
+            s = capi.from_workload(w, specialize=spec)
+            tau = s.tau
+            s.run(4 * tau)
+            b = capi.Batch([s], block=128)
+            b.run([9 * tau])
+            b.close()
+            s.run(w.t_end)
+            ref = capi.from_workload(w, specialize=spec)
+            ref.run(4 * tau)
+            ref.run(9 * tau)
+            ref.run(w.t_end)
+            assert s.windows == ref.windows
+            assert np.array_equal(s.get_counts(), ref.get_counts()), (w.name, spec)
+
+
 @pytest.mark.parametrize("block", [128, 512])
 def test_specialised_batch_equals_members_alone(capi, block):
     """Members sharing one model structure (the box network, different sizes,

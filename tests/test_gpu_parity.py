@@ -243,6 +243,77 @@ def test_edge_large_counts_and_p_equal_one(capi):
     assert np.array_equal(gc, oc) and gc.sum() == 100000
 
 
+def max_size_model(seed: int = 17):
+    """32 species and 32 reactions, the most a model may have: order-0 influx
+    (one masked to a region), a dimerisation 2X -> Y, reactions that change 6
+    species (the most one may), species 31 as a reactant, immobile species,
+    and seeded first- and second-order conversions for the rest."""
+    rng = np.random.default_rng(seed)
+    S = 32
+    names = [f"X{i}" for i in range(S)]
+    diff = np.exp(rng.uniform(np.log(1e-13), np.log(1e-11), S))
+    diff[[7, 19, 28]] = 0.0
+    rx = [([], ["X0"], 2e-4), ([], ["X1"], 5e-5), (["X2", "X2"], ["X3"], 3e6),
+          (["X4", "X5"], ["X6", "X7", "X8", "X9"], 2e6), (["X31"], ["X30", "X29", "X28", "X27", "X26"], 40.0)]
+    while len(rx) < 32:
+        if len(rx) % 2:
+            x, y = rng.choice(S, 2, replace=False)
+            rx.append(([names[x]], [names[y]], float(np.exp(rng.uniform(np.log(1.0), np.log(300.0))))))
+        else:
+            x, y, z = rng.choice(S, 3, replace=False)
+            rx.append(([names[x], names[y]], [names[z]], float(np.exp(rng.uniform(np.log(1e5), np.log(1e7))))))
+    return I.model_from_lists(names, list(diff), rx)
+
+
+@pytest.mark.parametrize("specialize,block", [(-1, 256), (-1, 512), (1, 256), (1, 128), (1, 512)])
+def test_edge_maximum_model_size_bit_exact(capi, specialize, block):
+    """S = 32, R = 32 on an irregular mesh of 5,202 tets (tiles of 128-512
+    with a ragged tail), generic and specialised kernels, against the oracle."""
+    w = I.config2(nx=3, t_end=1.5e-3)
+    m = max_size_model()
+    rng = np.random.default_rng(5)
+    c = rng.poisson(3.0, size=(32, w.n_tets)).astype(np.int32)
+    mask = np.zeros(w.n_tets, np.uint8)
+    mask[: w.n_tets // 7] = 1
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, m, c, 9, [0.4e-3, w.t_end], masks={0: mask},
+                            specialize=specialize, block=block)
+    assert g.specialized == (specialize == 1)
+    assert o.events > 0 and g.windows >= 3
+    assert np.array_equal(gc, oc)
+
+
+def test_sparse_rows_follow_molecules_across_tiles(capi):
+    """Molecules start in a few tets of a 10,404-tet mesh (41 tiles of 256,
+    most tiles empty at first) and spread over tiles: A diffuses fast,
+    converts to a slower B and to an immobile C. New molecules are added
+    between runs (counts reset on the device) and each run is compared with
+    the oracle."""
+    w = I.config2(nx=6, t_end=6e-3)
+    m = I.model_from_lists(["A", "B", "C"], [1e-11, 2e-12, 0.0],
+                           [(["A"], ["B"], 300.0), (["B"], ["C"], 100.0)])
+    c = np.zeros((3, w.n_tets), np.int32)
+    c[0, w.n_tets - 1] = 5000
+    c[0, np.random.default_rng(8).choice(w.n_tets, 6, replace=False)] = 800
+    for spec in (-1, 1):
+        g = capi.Simulation(w.verts, w.tets, m, 13, specialize=spec)
+        o = oracle.OracleSim(w.verts, w.tets, m, seed=13, prec=32)
+        for obj in (g, o):
+            obj.set_counts(c)
+        t = 0.0
+        for k, dt in enumerate([1.7e-3, 2.0e-3, 2.3e-3]):
+            t += dt
+            g.run(t)
+            o.run(t)
+            gc, oc = g.get_counts(), o.get_counts()
+            assert np.array_equal(gc, oc), (spec, k)
+            # a fresh species-A pulse in the first tet, on top of the state
+            nc = gc.copy()
+            nc[0, 0] += 3000
+            g.set_counts(nc)
+            o.set_counts(nc)
+        assert (g.get_counts()[2] > 0).sum() > 150
+
+
 def test_edge_noop_and_bad_arguments(capi):
     w = I.config1()
     s = capi.from_workload(w)
