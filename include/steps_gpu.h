@@ -199,6 +199,9 @@ int steps_run_record(steps_sim *sim, double t_end, double dt_rec, int32_t n_spec
  * results bit for bit; the specialised one takes fewer instructions. */
 int steps_sim_specialized(const steps_sim *sim, int32_t *specialized);
 
+/* Tets and species of a simulation (either output may be NULL). */
+int steps_sim_shape(const steps_sim *sim, int64_t *nt, int32_t *n_species);
+
 int steps_get_time(const steps_sim *sim, double *t);
 int steps_get_tau(const steps_sim *sim, double *tau);
 /* Windows run so far (the RNG window index) and kernel launches issued. */
@@ -255,6 +258,80 @@ int steps_batch_info(const steps_batch *batch, int32_t *block, uint64_t *launche
 
 /* *specialized = 1 when the batch runs the model-specialised batched kernel. */
 int steps_batch_specialized(const steps_batch *batch, int32_t *specialized);
+
+/* ---------------------------------------------------------------------- */
+/* Served form: continuous batching of simulation jobs on one GPU.        */
+/* ---------------------------------------------------------------------- */
+typedef struct steps_server steps_server;
+
+typedef struct steps_server_options {
+    int64_t device_budget; /* bytes of device memory the running jobs may hold; 0 = no limit (default) */
+    int32_t max_jobs;      /* jobs advanced together; default 64 */
+    int32_t wave_windows;  /* windows of its own tau a job advances per round; default 16 */
+    int32_t block;         /* threads per block of the batched kernel; default 256 (fixed: batches re-form
+                              whenever jobs come and go, so no autotuning) */
+    int32_t specialize;    /* as steps_batch_options.specialize; default -1 (the generic batched kernel, no
+                              run-time compilation between requests) */
+    int32_t reserved[2];   /* set to 0 */
+} steps_server_options;
+
+void steps_server_options_default(steps_server_options *opt);
+
+/*
+ * A server that advances many independent jobs together with batched
+ * launches (the batched form above), admitting and retiring jobs between
+ * rounds. Jobs are admitted first come first served while a slot is free and
+ * the job's device memory fits the budget (a job is always admitted when none
+ * runs). Because every random number is addressed by (job seed, window,
+ * original tet), a job's result is the same bits as the same simulation run
+ * alone with steps_run, whatever else runs beside it.
+ * cuda_stream: stream of the server's launches (NULL = legacy default stream).
+ * Errors: STEPS_ERR_ARG (NULL, max_jobs < 1, wave_windows < 1, bad block).
+ */
+int steps_server_create(const steps_server_options *opt, void *cuda_stream, steps_server **out);
+/* Frees every job's device memory and results. */
+void steps_server_destroy(steps_server *srv);
+
+/*
+ * Queue a job: a simulation with the mesh, model, options, region masks and
+ * device tables of `proto` (steps_sim_clone: no host-side rebuilding), the
+ * job's own seed, initial counts `counts` ([n_species * nt] int32, species-
+ * major, original tet order, host; copied here) at time 0, run to t_end
+ * seconds. `proto` must stay alive until the job is admitted (see
+ * steps_server_job_state). *job: the job's id (0, 1, 2, ... in submission
+ * order). Errors: STEPS_ERR_ARG (NULL, t_end not finite or < 0).
+ */
+int steps_server_submit(steps_server *srv, const steps_sim *proto, uint64_t seed, const int32_t *counts,
+                        double t_end, int64_t *job);
+
+/*
+ * One round: admit queued jobs; advance every running job by up to
+ * wave_windows windows on its own window grid, stopping at its t_end (one
+ * batched run; the batch is re-formed only when the set of running jobs
+ * changed); retire the jobs that reached t_end (final counts copied to the
+ * host, device memory freed). *running: jobs running after the round;
+ * *finished: jobs that finished in this round (either may be NULL).
+ * Synchronises with the server's stream. Errors as steps_batch_run; jobs
+ * keep their state.
+ */
+int steps_server_step(steps_server *srv, int32_t *running, int32_t *finished);
+
+/* State of a job: 0 queued, 1 running, 2 finished (result held), 3 result
+ * taken; its windows run so far and its simulated time. Any output may be
+ * NULL. Errors: STEPS_ERR_ARG (unknown job). */
+int steps_server_job_state(const steps_server *srv, int64_t job, int32_t *state, uint64_t *windows, double *t);
+
+/* Final counts of a finished job ([n_species * nt] int32, original tet order,
+ * host, caller-owned, sized by the job's prototype); the server then frees
+ * its copy. counts_out may be NULL to free it unread. Errors: STEPS_ERR_ARG
+ * (unknown job), STEPS_ERR_STATE (not finished, or already taken). */
+int steps_server_take_result(steps_server *srv, int64_t job, int32_t *counts_out);
+
+/* Rounds run, batch re-formations, batched kernel launches, jobs queued and
+ * running now, and the device bytes the running jobs hold. Any output may be
+ * NULL. */
+int steps_server_stats(const steps_server *srv, uint64_t *rounds, uint64_t *rebuilds, uint64_t *launches,
+                       int32_t *queued, int32_t *running, int64_t *device_bytes);
 
 /*
  * Advance `sim` to t_end on counts held in a caller-owned device buffer,

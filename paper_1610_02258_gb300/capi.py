@@ -31,7 +31,9 @@ EXPORTS = [
     "steps_last_error", "steps_debug_philox", "steps_debug_logf", "steps_run_noalloc",
     "steps_batch_options_default", "steps_batch_create", "steps_batch_destroy", "steps_batch_run",
     "steps_batch_info", "steps_sim_clone", "steps_sim_device_bytes", "steps_set_reac_rate", "steps_run_record",
-    "steps_sim_specialized", "steps_batch_specialized",
+    "steps_sim_specialized", "steps_batch_specialized", "steps_sim_shape",
+    "steps_server_options_default", "steps_server_create", "steps_server_destroy", "steps_server_submit",
+    "steps_server_step", "steps_server_job_state", "steps_server_take_result", "steps_server_stats",
 ]
 
 
@@ -49,6 +51,11 @@ class steps_options(ctypes.Structure):
 class steps_batch_options(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("specialize", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 5)]
+
+
+class steps_server_options(ctypes.Structure):
+    _fields_ = [("device_budget", ctypes.c_int64), ("max_jobs", ctypes.c_int32), ("wave_windows", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("specialize", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 def _load():
@@ -90,6 +97,18 @@ def _load():
         "steps_set_reac_rate": (ctypes.c_int, [P, i32, ctypes.c_double]),
         "steps_sim_specialized": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
         "steps_batch_specialized": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
+        "steps_sim_shape": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+        "steps_server_options_default": (None, [ctypes.POINTER(steps_server_options)]),
+        "steps_server_create": (ctypes.c_int, [ctypes.POINTER(steps_server_options), P, PP]),
+        "steps_server_destroy": (None, [P]),
+        "steps_server_submit": (ctypes.c_int, [P, P, u64, P, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]),
+        "steps_server_step": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+        "steps_server_job_state": (ctypes.c_int, [P, i64, ctypes.POINTER(ctypes.c_int32),
+                                                  ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
+        "steps_server_take_result": (ctypes.c_int, [P, i64, P]),
+        "steps_server_stats": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
         "steps_run_record": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_double, i32, P, i32, P, P, i64,
                                             ctypes.POINTER(ctypes.c_int64)]),
     }
@@ -331,6 +350,69 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             steps_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+class NativeServer:
+    """The library's job server (steps_server_*): jobs are clones of prototype
+    Simulation objects, advanced together in batched rounds."""
+
+    def __init__(self, device_budget=0, max_jobs=64, wave_windows=16, block=256, specialize=-1, cuda_stream=None):
+        opt = steps_server_options()
+        lib.steps_server_options_default(ctypes.byref(opt))
+        opt.device_budget = int(device_budget)
+        opt.max_jobs = int(max_jobs)
+        opt.wave_windows = int(wave_windows)
+        opt.block = int(block)
+        opt.specialize = int(specialize)
+        h = ctypes.c_void_p()
+        _check(lib.steps_server_create(ctypes.byref(opt), ctypes.c_void_p(cuda_stream) if cuda_stream else None,
+                                       ctypes.byref(h)))
+        self._h = h
+        self._shape = {}
+
+    def submit(self, proto, seed, counts, t_end):
+        """Queue a job on prototype `proto` (a Simulation) from counts [S, nt]
+        at time 0 to t_end; returns the job id."""
+        c = np.ascontiguousarray(counts, np.int32)
+        if c.shape != (proto.S, proto.nt):
+            raise ValueError(f"counts must have shape {(proto.S, proto.nt)}")
+        job = ctypes.c_int64()
+        _check(lib.steps_server_submit(self._h, proto._sim, int(seed), _ptr(c), float(t_end), ctypes.byref(job)))
+        self._shape[job.value] = c.shape
+        return job.value
+
+    def step(self):
+        """One round; returns (jobs running, jobs finished in the round)."""
+        r, f = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.steps_server_step(self._h, ctypes.byref(r), ctypes.byref(f)))
+        return r.value, f.value
+
+    def state(self, job):
+        """(state, windows, time): state 0 queued, 1 running, 2 finished, 3 result taken."""
+        st, w, t = ctypes.c_int32(), ctypes.c_uint64(), ctypes.c_double()
+        _check(lib.steps_server_job_state(self._h, int(job), ctypes.byref(st), ctypes.byref(w), ctypes.byref(t)))
+        return st.value, w.value, t.value
+
+    def take_result(self, job):
+        out = np.empty(self._shape.pop(job), np.int32)
+        _check(lib.steps_server_take_result(self._h, int(job), _ptr(out)))
+        return out
+
+    def stats(self):
+        r, b, l = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        q, n, by = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(lib.steps_server_stats(self._h, ctypes.byref(r), ctypes.byref(b), ctypes.byref(l), ctypes.byref(q),
+                                      ctypes.byref(n), ctypes.byref(by)))
+        return {"rounds": r.value, "rebuilds": b.value, "launches": l.value, "queued": q.value,
+                "running": n.value, "device_bytes": by.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.steps_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

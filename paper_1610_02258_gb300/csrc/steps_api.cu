@@ -778,6 +778,13 @@ int steps_get_tau(const steps_sim *sim, double *tau) {
     return STEPS_OK;
 }
 
+int steps_sim_shape(const steps_sim *sim, int64_t *nt, int32_t *n_species) {
+    CHECK_NULL(sim, "steps_sim_shape");
+    if (nt) *nt = sim->T;
+    if (n_species) *n_species = sim->S;
+    return STEPS_OK;
+}
+
 int steps_get_windows(const steps_sim *sim, uint64_t *windows, uint64_t *launches) {
     CHECK_NULL(sim, "steps_get_windows");
     if (windows) *windows = sim->k_total;

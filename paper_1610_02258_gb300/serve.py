@@ -1,17 +1,14 @@
 """Served form: continuous batching of simulation jobs on one GPU.
 
-Host-side scheduling only; every window runs in the CUDA library through the
-C ABI (batched launches). Jobs (mesh generator, size, seed, t_end) arrive
-over time; a job is admitted, first come first served, when its device
-memory fits the budget and a slot is free; its counts and random-number
-state stay resident on the device until it finishes. The server advances all
-admitted jobs together in waves: each wave is one batched run that moves
-every job by up to `wave_windows` windows of its own length, stopping on the
-job's window grid (so no extra shortened windows are inserted) or at its
-t_end. Jobs that finish leave between waves and their memory is freed; jobs
-that arrived meanwhile join the next wave. Because every draw is addressed by
-(job seed, window, tet), a job's result is the same bits whether it runs
-alone or in any mix.
+The scheduling is the library's (steps_server_*): jobs are clones of a
+prototype simulation, admitted first come first served when a slot is free
+and their device memory fits the budget, advanced together in rounds (one
+batched run moves every job by up to `wave_windows` windows of its own
+length, stopping on its window grid or at its t_end) and retired between
+rounds. This module supplies the job stream (mesh generator, size, seed,
+t_end, arrival time), feeds arrived jobs to the server and records
+latencies. Because every draw is addressed by (job seed, window, tet), a
+job's result is the same bits whether it runs alone or in any mix.
 """
 from __future__ import annotations
 
@@ -82,6 +79,11 @@ def _new_job_sim(protos, spec):
 
 
 class Server:
+    """Feeds a stream of jobs, by arrival time, to the library's job server
+    (steps_server_*: admission by slots and device-memory budget, batched
+    rounds, retirement; all of it native) and collects each job's result and
+    latency. The budget covers the prototypes and the running jobs."""
+
     def __init__(self, hbm_budget: int, max_jobs: int = 64, wave_windows: int = 16, block: int = 256,
                  cuda_stream=None, specialize: int = -1):
         self.budget = int(hbm_budget)
@@ -100,72 +102,51 @@ class Server:
         """Serve `jobs` (list of JobSpec, by arrival). Returns {job_id: JobResult}."""
         pending = sorted(jobs, key=lambda j: j.arrival)
         results = {j.job_id: JobResult(j.job_id, j.arrival) for j in jobs}
-        active = []  # (spec, sim)
-        batch = None
-        members_key = None
-        t0 = time.perf_counter()
-        nxt = 0
-        while nxt < len(pending) or active:
-            now = time.perf_counter() - t0
-            # admission: arrived jobs, first come first served, by memory budget and slots
-            used = self.protos.device_bytes() + sum(s.device_bytes for _, s in active)
-            while nxt < len(pending) and (not realtime or pending[nxt].arrival <= now) and len(active) < self.max_jobs:
-                spec = pending[nxt]
-                proto = self.protos.sim(spec.kind, spec.size)
-                need = proto.device_bytes
-                used = self.protos.device_bytes() + sum(s.device_bytes for _, s in active)
-                if active and used + need > self.budget:
-                    self.stats["admit_waits"] += 1
-                    break
-                s = _new_job_sim(self.protos, spec)
-                results[spec.job_id].start = time.perf_counter() - t0
-                results[spec.job_id].tets = s.nt
-                active.append((spec, s))
-                nxt += 1
-            if not active:
-                if realtime and nxt < len(pending):
-                    time.sleep(max(0.0, pending[nxt].arrival - (time.perf_counter() - t0)))
-                continue
-            self.stats["max_active"] = max(self.stats["max_active"], len(active))
-            key = tuple(id(s) for _, s in active)
-            if key != members_key:
-                if batch is not None:
-                    self.stats["launches"] += batch.info[1]
-                    batch.close()
-                batch = capi.Batch([s for _, s in active], block=self.block, cuda_stream=self.stream,
-                                   specialize=self.specialize)
-                members_key = key
-                self.stats["batch_rebuilds"] += 1
-            # one wave: every job by up to wave_windows windows on its own grid
-            targets = []
-            for spec, s in active:
-                t = s.time
-                tgt = t + self.wave_windows * s.tau if np.isfinite(s.tau) else spec.t_end
-                targets.append(min(spec.t_end, tgt))
-            batch.run(targets)
-            self.stats["waves"] += 1
-            # retire finished jobs
-            keep = []
-            for spec, s in active:
-                if s.time >= spec.t_end - 1e-12 * max(spec.t_end, 1e-30):
-                    r = results[spec.job_id]
-                    r.counts = s.get_counts()
-                    r.windows = s.windows
-                    r.finish = time.perf_counter() - t0
-                    s.close()
-                else:
-                    keep.append((spec, s))
-            if len(keep) != len(active):
-                if batch is not None:
-                    self.stats["launches"] += batch.info[1]
-                    batch.close()
-                batch = None
-                members_key = None
-            active = keep
-        if batch is not None:
-            self.stats["launches"] += batch.info[1]
-            batch.close()
-        self.stats["makespan"] = time.perf_counter() - t0
+        for j in pending:  # meshes and tables of every kind of job, before the clock starts
+            self.protos.sim(j.kind, j.size)
+        native = capi.NativeServer(device_budget=max(1, self.budget - self.protos.device_bytes()),
+                                   max_jobs=self.max_jobs, wave_windows=self.wave_windows, block=self.block,
+                                   specialize=self.specialize, cuda_stream=self.stream)
+        try:
+            outstanding = {}  # native job id -> JobSpec
+            t0 = time.perf_counter()
+            nxt = 0
+            while nxt < len(pending) or outstanding:
+                now = time.perf_counter() - t0
+                while nxt < len(pending) and (not realtime or pending[nxt].arrival <= now):
+                    spec = pending[nxt]
+                    proto = self.protos.sim(spec.kind, spec.size)
+                    w = self.protos.workload(spec.kind, spec.size)
+                    outstanding[native.submit(proto, spec.seed, w.counts, spec.t_end)] = spec
+                    results[spec.job_id].tets = proto.nt
+                    nxt += 1
+                if not outstanding:
+                    if realtime and nxt < len(pending):
+                        time.sleep(max(0.0, pending[nxt].arrival - (time.perf_counter() - t0)))
+                    continue
+                running, _ = native.step()
+                st = native.stats()
+                self.stats["max_active"] = max(self.stats["max_active"], running)
+                if st["queued"] > 0 and running < self.max_jobs:
+                    self.stats["admit_waits"] += 1  # the memory budget held jobs back
+                now = time.perf_counter() - t0
+                for nid in list(outstanding):
+                    state, windows, _ = native.state(nid)
+                    r = results[outstanding[nid].job_id]
+                    if state >= 1 and r.start == 0.0:
+                        r.start = now
+                    if state == 2:
+                        r.counts = native.take_result(nid)
+                        r.windows = windows
+                        r.finish = now
+                        del outstanding[nid]
+            self.stats["makespan"] = time.perf_counter() - t0
+            st = native.stats()
+            self.stats["waves"] = st["rounds"]
+            self.stats["batch_rebuilds"] = st["rebuilds"]
+            self.stats["launches"] = st["launches"]
+        finally:
+            native.close()
         return results
 
     def close(self):

@@ -87,3 +87,30 @@ def test_model_validation(capi):
     with pytest.raises(capi.StepsError) as e:  # too many species
         capi.steps_model_create(np.zeros(33), np.zeros((0, 33)), np.zeros((0, 33)), np.zeros(0))
     assert e.value.code == -1
+
+
+def test_server_host_side_arguments(capi):
+    """The job server's options, empty rounds and job lookups are host work."""
+    import ctypes
+    lib = capi.lib
+    o = capi.steps_server_options()
+    lib.steps_server_options_default(ctypes.byref(o))
+    assert (o.device_budget, o.max_jobs, o.wave_windows, o.block, o.specialize) == (0, 64, 16, 256, -1)
+    h = ctypes.c_void_p()
+    assert lib.steps_server_create(ctypes.byref(o), None, ctypes.byref(h)) == 0 and h.value
+    r, f = ctypes.c_int32(-1), ctypes.c_int32(-1)
+    assert lib.steps_server_step(h, ctypes.byref(r), ctypes.byref(f)) == 0 and (r.value, f.value) == (0, 0)
+    assert lib.steps_server_job_state(h, 0, None, None, None) == -1
+    assert lib.steps_server_take_result(h, 0, None) == -1
+    job = ctypes.c_int64()
+    assert lib.steps_server_submit(h, None, 1, None, 1e-3, ctypes.byref(job)) == -1
+    q = ctypes.c_int32(-1)
+    assert lib.steps_server_stats(h, None, None, None, ctypes.byref(q), None, None) == 0 and q.value == 0
+    lib.steps_server_destroy(h)
+    for field, bad in [("max_jobs", 0), ("wave_windows", 0), ("block", 96), ("specialize", 2), ("device_budget", -1)]:
+        b = capi.steps_server_options()
+        lib.steps_server_options_default(ctypes.byref(b))
+        setattr(b, field, bad)
+        h2 = ctypes.c_void_p()
+        assert lib.steps_server_create(ctypes.byref(b), None, ctypes.byref(h2)) == -1, field
+    assert lib.steps_server_create(None, None, None) == -1

@@ -48,3 +48,41 @@ def test_each_job_same_alone_and_in_the_mix(serve, realtime):
     s = serve.summarize(mixed, srv.stats["makespan"])
     assert s["jobs"] == len(jobs) and s["p99_s"] >= s["p50_s"] > 0
     protos.close()
+
+
+def test_native_server_jobs_equal_alone_and_budget_admission(serve):
+    """steps_server_* directly: jobs on three prototypes (1,920-tet cuboid,
+    box, small dendrite) with end times on and off the window grid and one of
+    0; each result equals the same simulation run alone with steps_run. A
+    budget below two jobs admits one job at a time; a result is taken once."""
+    from paper_1610_02258_gb300 import capi
+    ws = [I.config1(seed=3), I.config2(seed=9, nx=3, t_end=2e-3), I.config3(h=0.5e-6, t_end=0.1e-3)]
+    protos = [capi.from_workload(w) for w in ws]
+    specs = [(0, 11, 3.3e-3), (1, 12, 2.0e-3), (2, 13, 0.1e-3), (1, 14, 0.0), (0, 15, 1.48e-3), (2, 16, 0.071e-3)]
+    for budget, limit in [(0, 6), (1, 1)]:
+        srv = capi.NativeServer(device_budget=budget, max_jobs=4, wave_windows=5)
+        ids = [srv.submit(protos[k], seed, ws[k].counts, t) for k, seed, t in specs]
+        assert ids == list(range(len(specs)))
+        assert all(srv.state(i)[0] == 0 for i in ids)
+        most = 0
+        for _ in range(10000):
+            running, _ = srv.step()
+            most = max(most, running)
+            if all(srv.state(i)[0] == 2 for i in ids):
+                break
+        assert most <= min(limit, 4)
+        for i, (k, seed, t) in zip(ids, specs):
+            state, windows, tt = srv.state(i)
+            assert state == 2 and abs(tt - t) <= 1e-9 * t
+            got = srv.take_result(i)
+            ref = protos[k].clone(seed)
+            ref.set_counts(ws[k].counts)
+            ref.run(t)
+            assert windows == ref.windows
+            assert np.array_equal(got, ref.get_counts()), (budget, i)
+            assert srv.state(i)[0] == 3
+            with pytest.raises(capi.StepsError):
+                capi._check(capi.lib.steps_server_take_result(srv._h, i, None))
+        st = srv.stats()
+        assert st["running"] == 0 and st["queued"] == 0 and st["device_bytes"] == 0
+        srv.close()
