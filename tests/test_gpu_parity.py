@@ -59,6 +59,36 @@ def test_philox_bit_exact(capi):
         assert np.array_equal(capi.steps_debug_philox(seed, ctr), oracle.philox_array(seed, ctr))
 
 
+def test_philox_equals_curand_device_generator(capi, tmp_path_factory):
+    """Both Philox4x32-10 implementations (device, oracle) against cuRAND's
+    device Philox4x32-10 (curand_kernel.h) for the same key and counters."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+    nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    if not os.path.exists(nvcc):
+        nvcc = shutil.which("nvcc")
+    if not nvcc:
+        pytest.skip("nvcc not found")
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cuda", "curand_philox.cu")
+    lib = str(tmp_path_factory.mktemp("curand") / "libcurand_philox.so")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-shared", "-Xcompiler", "-fPIC",
+                    "-o", lib, src], check=True, capture_output=True)
+    L = ctypes.CDLL(lib)
+    L.curand_philox.argtypes = [ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    rng = np.random.default_rng(11)
+    ctr = rng.integers(0, 2**32, size=(1 << 14, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    ctr[2] = [5, 0, 0, 0]
+    for seed in [0, 3, (1 << 64) - 1, 0x0123456789ABCDEF]:
+        ref = np.empty_like(ctr)
+        assert L.curand_philox(seed, ctr.ctypes.data, ctr.shape[0], ref.ctypes.data) == 0
+        assert np.array_equal(capi.steps_debug_philox(seed, ctr), ref)
+        assert np.array_equal(oracle.philox_array(seed, ctr), ref)
+
+
 def test_logf_bit_exact_on_every_uniform(capi):
     """The kernel's float log agrees bit for bit with the oracle's on all 2^24
     uniforms (m+1)/2^24 the reaction operator can draw, and on random floats."""
