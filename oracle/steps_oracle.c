@@ -23,7 +23,7 @@
  * tau = 1 / max_{S,tet} d_{S,tet} (§2.1); the last window of a run is cut to
  * t_end - t (Algorithm 1).
  *
- * Readings of points the paper leaves open (all also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - d_{S,tet} = sum over internal faces f of D_S * A_f / (V_tet * d_f), with
  *     d_f the distance between the two tets' barycentres; boundary faces are
  *     reflective. tau is the min over diffusive species only.
