@@ -139,3 +139,31 @@ def test_specialised_batch_of_many_species_models(capi):
     b.run([w.t_end for w in ws])
     for ref, m in zip(alone, members):
         assert np.array_equal(m.get_counts(), ref)
+
+
+def test_full_size_batched_configuration_sampled_against_oracle(capi):
+    """The batched benchmark configuration at full size: 256 box replicates
+    of 10k-300k tets (20.1M tets), block size autotuned on the first run, the
+    model-specialised batched kernel. After 3 ms (about 15 windows each, 12 of
+    them inside the autotuner) four members (the smallest, the largest and two
+    seeded picks) equal the oracle run on that member alone."""
+    import oracle
+    sizes = I.batch_sizes(n=256)
+    ws = [I.box_for_tets(int(sz), seed=1000 + j) for j, sz in enumerate(sizes)]
+    sims = [capi.from_workload(w) for w in ws]
+    assert sum(s.nt for s in sims) > 20_000_000
+    b = capi.Batch(sims, block=0)
+    t_end = 3e-3
+    b.run([t_end] * len(sims))
+    assert b.specialized
+    assert b.info[0] in (128, 256, 512) and max(b.info[2]) > 0  # the autotuner ran
+    nts = np.array([s.nt for s in sims])
+    picks = {int(nts.argmin()), int(nts.argmax())} | set(np.random.default_rng(4).choice(256, 2, replace=False).tolist())
+    for j in sorted(picks):
+        w = ws[j]
+        o = oracle.OracleSim(w.verts, w.tets, w.model, seed=w.seed, prec=32)
+        o.set_counts(w.counts)
+        o.run(t_end)
+        assert sims[j].windows == o.windows
+        assert np.array_equal(sims[j].get_counts(), o.get_counts()), j
+    b.close()
