@@ -572,12 +572,19 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         const uint32_t n4 = ((uint32_t)nlive + 3u) & ~3u;
         for (int s = 0; s < S; ++s) bulk_g2s(cnt_all + s * BLOCK, a.cur + s * Tpad + i0, n4 * 4u, &bar);
         // the tile `prefetch` tiles ahead, processed about one resident wave
-        // later, into L2
-        const int64_t p0 = i0 + (int64_t)a.prefetch * BLOCK;
-        if (a.prefetch > 0 && p0 < a.T) {
+        // later, into L2. The last wave's blocks take the next window's first
+        // tiles, from the buffer that window reads (lines that this window's
+        // atomics still change are only brought into L2, where they land).
+        int64_t p0 = i0 + (int64_t)a.prefetch * BLOCK;
+        const int32_t *pc = a.cur;
+        if (p0 >= a.T) {
+            p0 -= ((int64_t)a.T + BLOCK - 1) / BLOCK * BLOCK;
+            pc = a.nxt;
+        }
+        if (a.prefetch > 0 && p0 >= 0 && p0 < a.T) {
             const uint32_t pl = (uint32_t)min((int64_t)BLOCK, (int64_t)a.T - p0);
             const uint32_t p4 = (pl + 3u) & ~3u;
-            for (int s = 0; s < S; ++s) bulk_prefetch_l2(a.cur + s * Tpad + p0, p4 * 4u);
+            for (int s = 0; s < S; ++s) bulk_prefetch_l2(pc + s * Tpad + p0, p4 * 4u);
             bulk_prefetch_l2(a.thr + p0, pl * 16u);
             bulk_prefetch_l2(a.nbr + p0, pl * 16u);
             bulk_prefetch_l2(a.inv_nav + p0, p4 * 4u);
