@@ -163,7 +163,7 @@ struct steps_sim {
         a.tau_dn = (float)tau_k;
         if ((double)a.tau_dn > tau_k) a.tau_dn = std::nextafter(a.tau_dn, 0.0f);
         a.occ = opt.occupancy;
-        a.prefetch = 1;  // launch_step sets the distance: one resident wave
+        a.prefetch = 1;  // the launch sets the distance: half a resident wave
         a.trial = d_trial;
         std::memcpy(a.scale, scale, sizeof(a.scale));
         return a;

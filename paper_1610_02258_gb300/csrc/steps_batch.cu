@@ -32,9 +32,9 @@ int launch_batch_t(const BlockWork *work, int64_t nblocks, RepEntry *reps, int m
             return STEPS_ERR_CUDA;
         }
     }
-    // L2 prefetch about one resident wave ahead (the work list runs through a
+    // L2 prefetch about half a resident wave ahead (the work list runs through a
     // member's tiles in order)
-    const int32_t prefetch = resident_blocks(reinterpret_cast<const void *>(step_kernel_batch<BLOCK, RM, Z>), BLOCK, smem);
+    const int32_t prefetch = prefetch_distance(reinterpret_cast<const void *>(step_kernel_batch<BLOCK, RM, Z>), BLOCK, smem);
     step_kernel_batch<BLOCK, RM, Z><<<(unsigned)nblocks, BLOCK, smem, (cudaStream_t)stream>>>(work, reps, prefetch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

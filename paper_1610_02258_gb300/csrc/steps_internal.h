@@ -52,9 +52,10 @@ void build_tables(const HostMesh &mesh, const HostModel &model, int reorder, Tab
 uint32_t species_scale(const HostModel &model, const Tables &t, int s, double tau_k);
 
 // steps_kernels.cu
-// Blocks of a kernel resident on the whole GPU at once (SMs x blocks per SM),
-// cached per kernel and shared-memory size; the L2 prefetch distance.
-int resident_blocks(const void *kernel, int block, size_t smem);
+// L2 prefetch distance in tiles: half of the blocks of a kernel resident on
+// the whole GPU at once (SMs x blocks per SM), cached per kernel and
+// shared-memory size.
+int prefetch_distance(const void *kernel, int block, size_t smem);
 int launch_step(const ModelDev &m, const StepArgs &a, int block, void *stream);
 int launch_philox_test(uint64_t seed, const uint32_t *d_ctr, int64_t n, uint32_t *d_out, void *stream);
 int launch_logf_test(const float *d_x, int64_t n, float *d_out, void *stream);

@@ -48,8 +48,8 @@ int launch_step_t(const ModelDev &m, const StepArgs &a, void *stream) {
     }
     StepArgs b = a;
     if (b.prefetch) {
-        // about one resident wave ahead
-        b.prefetch = resident_blocks(reinterpret_cast<const void *>(step_kernel<BLOCK, RM, Z>), BLOCK, smem);
+        // about half a resident wave ahead
+        b.prefetch = prefetch_distance(reinterpret_cast<const void *>(step_kernel<BLOCK, RM, Z>), BLOCK, smem);
     }
     // programmatic dependent launch: overlaps this window's set-up with the
     // previous window's tail (the kernel waits for it before reading counts)
@@ -89,7 +89,7 @@ int launch_step_b(const ModelDev &m, const StepArgs &a, void *stream) {
 
 }  // namespace
 
-int resident_blocks(const void *kernel, int block, size_t smem) {
+int prefetch_distance(const void *kernel, int block, size_t smem) {
     struct Entry {
         const void *k;
         size_t smem;
@@ -102,7 +102,9 @@ int resident_blocks(const void *kernel, int block, size_t smem) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
-    const int n = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    // half a resident wave (SMs x resident blocks per SM / 2): on the 1.03M-tet
+    // dendrite, 0.125 to 3 waves were timed and half a wave was fastest
+    const int n = std::max(1, (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) / 2);
     static thread_local int next = 0;
     cache[next] = Entry{kernel, smem, n};
     next = (next + 1) & 7;

@@ -78,7 +78,7 @@ Nvrtc &nvrtc() {
 }  // namespace
 
 // Models with many species keep the trial counts in a global buffer: their
-// tile's shared memory then fits four resident blocks per SM.
+// tile's shared memory then fits more resident blocks per SM.
 bool spec_global_trial(const HostModel &hm) { return hm.dev.S >= 16; }
 
 namespace {
@@ -140,8 +140,13 @@ int reaction_bucket(int R) { return R <= 8 ? 8 : R <= 16 ? 16 : R <= 24 ? 24 : 3
 
 std::string program_source(const HostModel &hm, int block) {
     std::ostringstream o;
+    // models with many species keep trial counts in global memory; at 256
+    // threads their tiles then fit five resident blocks per SM with a 32-entry
+    // block map and 48 registers per thread
+    const bool five = spec_global_trial(hm) && block == 256;
+    if (five) o << "#define STEPS_MAP_CAP 32\n";
     o << "#include \"steps_step.cuh\"\n" << policy_source(hm, block);
-    o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << 2048 / block / 2 << ")\n"
+    o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << (five ? 5 : 2048 / block / 2) << ")\n"
       << "steps_spec_step(const __grid_constant__ steps::ModelDev m, const __grid_constant__ steps::StepArgs a) {\n"
       << "    steps::step_tile<" << block << ", " << reaction_bucket(hm.dev.R) << ", steps::SpecModel>(m, a, "
       << "(int64_t)blockIdx.x);\n}\n";
@@ -255,7 +260,7 @@ int launch_spec(void *spec, const ModelDev &m, const StepArgs &a, int block, voi
     const size_t smem = ((size_t)m.S + 1 + (c->global_trial ? 0 : (size_t)m.S)) * (size_t)block * sizeof(int32_t);
     if (!opt_in(fn, smem, &c->smem_set)) return STEPS_ERR_CUDA;
     StepArgs b = a;
-    if (b.prefetch) b.prefetch = resident_blocks(fn, block, smem);
+    if (b.prefetch) b.prefetch = prefetch_distance(fn, block, smem);
     ModelDev mm = m;
     void *args[2] = {(void *)&mm, (void *)&b};
     const unsigned grid = (unsigned)((a.T + block - 1) / block);
@@ -285,7 +290,7 @@ int launch_spec_batch(void *spec, const BlockWork *work, int64_t nblocks, RepEnt
     const void *fn = (const void *)c->kern_batch;
     const size_t smem = ((size_t)S + 1 + (c->global_trial ? 0 : (size_t)S)) * (size_t)block * sizeof(int32_t);
     if (!opt_in(fn, smem, &c->smem_set_batch)) return STEPS_ERR_CUDA;
-    int32_t prefetch = resident_blocks(fn, block, smem);
+    int32_t prefetch = prefetch_distance(fn, block, smem);
     void *args[3] = {(void *)&work, (void *)&reps, (void *)&prefetch};
     cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)nblocks), dim3((unsigned)block), args, smem, (cudaStream_t)stream);
     if (e != cudaSuccess) {

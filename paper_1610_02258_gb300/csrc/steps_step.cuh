@@ -364,8 +364,13 @@ __device__ __forceinline__ void species_thresholds(const uint4 &A, uint32_t R, u
 // order), cut into Philox blocks of 4 words. Block b of the chunk belongs to
 // lane `owner` with first[lane] <= b < first[lane + 1]; the map caches the
 // owner, the species of the block's first word and the tet's trial
-// molecules before that species for the first kMapCap blocks.
-constexpr int kMapCap = 160;
+// molecules before that species for the first kMapCap blocks (a program may
+// set a smaller map to fit more resident blocks; blocks past it are found by
+// search).
+#ifndef STEPS_MAP_CAP
+#define STEPS_MAP_CAP 160
+#endif
+constexpr int kMapCap = STEPS_MAP_CAP;
 
 struct WarpWork {
     int16_t tet[32];          // tile index of each lane's tet (-1: none)
@@ -571,8 +576,8 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     if (tid == 0) {
         const uint32_t n4 = ((uint32_t)nlive + 3u) & ~3u;
         for (int s = 0; s < S; ++s) bulk_g2s(cnt_all + s * BLOCK, a.cur + s * Tpad + i0, n4 * 4u, &bar);
-        // the tile `prefetch` tiles ahead, processed about one resident wave
-        // later, into L2. The last wave's blocks take the next window's first
+        // the tile `prefetch` tiles ahead, processed about half a resident
+        // wave later, into L2. The last wave's blocks take the next window's first
         // tiles, from the buffer that window reads (lines that this window's
         // atomics still change are only brought into L2, where they land).
         int64_t p0 = i0 + (int64_t)a.prefetch * BLOCK;
