@@ -194,11 +194,17 @@ def measure_batched(args, capi, I, torch, peak):
     T = np.array([s.nt for s in sims], dtype=np.int64)
     S = ws[0].model.n_species
 
+    def reset():  # every step is the configured 20 ms run from the initial counts
+        for s, w in zip(sims, ws):
+            s.set_counts(w.counts)
+
     def step():
         batch.run([s.time + 20e-3 for s in sims])
 
+    reset()
     step()  # autotune + warm
     for _ in range(2):
+        reset()
         step()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
@@ -206,6 +212,7 @@ def measure_batched(args, capi, I, torch, peak):
     steps = max(2, min(args.steps, 5))
     ms = 0.0
     for _ in range(steps):
+        reset()
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -227,7 +234,8 @@ def measure_batched(args, capi, I, torch, peak):
            "windows_per_step_max": launches / steps, "block": blk, "autotune_ms_per_window": tune,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": traffic, "traffic_note": "ncu DRAM bytes per launch on 32 replicates, scaled by tets"},
-           "setup_s": setup_s, "l2": "working set > L2; also flushed before each step"}
+           "setup_s": setup_s, "l2": "working set > L2; also flushed before each step",
+           "step": "one batched run of 20 ms per member from its initial counts (reset outside the events)"}
     batch.close()
     for s in sims:
         s.close()
@@ -236,27 +244,30 @@ def measure_batched(args, capi, I, torch, peak):
 
 def measure_dendrite(args, capi, I, torch, peak):
     """Plain form on the dendrite workload: ~1M tets, 20-species calcium
-    network with masked influx, tau = 3.3 us. One step advances the simulation
-    by --dendrite-ms of simulated time (about 300 windows per ms). Its counts
-    and tables (~210 MB) exceed L2, so this is the HBM-bound case."""
+    network with masked influx, tau = 3.3 us. One step is the configured run:
+    --dendrite-ms of simulated time (default 50 ms, about 15,000 windows) from
+    the initial counts, reset outside the timed region. Its counts and tables
+    (~210 MB) exceed L2, so this is the HBM-bound case."""
     t0 = time.perf_counter()
     w = I.config3()
     stream = torch.cuda.current_stream()
     sim = capi.from_workload(w, cuda_stream=stream.cuda_stream)
     setup_s = time.perf_counter() - t0
     t_step = args.dendrite_ms * 1e-3
+    host_in = torch.from_numpy(np.ascontiguousarray(w.counts, np.int32)).pin_memory().numpy()
 
     def step():
         sim.run(sim.time + t_step)
 
-    for _ in range(3):
-        step()
+    capi.steps_set_counts_all(sim._sim, host_in)
+    step()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     w0, _ = capi.steps_get_windows(sim._sim)
-    steps = max(3, min(args.steps, 10))
+    steps = 2
     ms = 0.0
     for _ in range(steps):
+        capi.steps_set_counts_all(sim._sim, host_in)
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -278,40 +289,47 @@ def measure_dendrite(args, capi, I, torch, peak):
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": tr["bytes_per_launch"] if tr else None, "bytes_per_tet_update": bytes_per_tet,
                         "kernel_us_avg": kernel_s * 1e6, "issue": issue_roofline(tr, kernel_s, None)},
-           "setup_s": setup_s, "l2": "working set > L2; also flushed before each step"}
+           "setup_s": setup_s, "l2": "working set > L2; also flushed before each step",
+           "step": "steps_run over sim_ms_per_step from the initial counts (reset outside the events)"}
     sim.close()
     return out
 
 
 def measure_cuboid(args, capi, I, torch):
     """Plain form on the 1,920-tet cuboid (A + B <-> C, tau = 0.74 ms): the
-    launch-bound case. One step = 100 ms of simulated time (135 windows, replayed
-    from CUDA graphs)."""
+    launch-bound case. One step is the configured run, 10 ms of simulated time
+    (13 full windows and a shortened one) from the initial counts, reset
+    outside the timed region."""
     w = I.config1()
     stream = torch.cuda.current_stream()
     sim = capi.from_workload(w, cuda_stream=stream.cuda_stream)
-    t_step = 100e-3
+    t_step = w.t_end
+    host_in = np.ascontiguousarray(w.counts, np.int32)
 
     def step():
         sim.run(sim.time + t_step)
 
     for _ in range(3):
+        capi.steps_set_counts_all(sim._sim, host_in)
         step()
     torch.cuda.synchronize()
     w0, _ = capi.steps_get_windows(sim._sim)
     steps = max(5, min(args.steps, 20))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    ms = 0.0
     for _ in range(steps):
+        capi.steps_set_counts_all(sim._sim, host_in)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
     w1, _ = capi.steps_get_windows(sim._sim)
     windows = w1 - w0
     out = {"value": w.n_tets * windows / (ms / 1e3), "unit": UNIT, "workload": w.name, "tets": w.n_tets,
            "form": "plain", "kernel": "specialised" if sim.specialized else "generic",
            "sim_ms_per_step": t_step * 1e3, "windows_per_step": windows / steps, "us_per_window": 1e3 * ms / windows,
+           "step": "steps_run over sim_ms_per_step from the initial counts (reset outside the events)",
            "bound": "launch/latency (1,920 tets fill 8 blocks of 256)"}
     sim.close()
     return out
@@ -442,11 +460,18 @@ def run_ours(args):
     tau = sim.tau
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     t_step = args.sim_ms * 1e-3 if args.sim_ms > 0 else w.t_end
+    # pinned host copy of the initial counts: every step is the configured run,
+    # t_step of simulated time from the initial state
+    host_in = torch.from_numpy(np.ascontiguousarray(w.counts, np.int32)).pin_memory().numpy()
+
+    def reset():
+        capi.steps_set_counts_all(sim._sim, host_in)
 
     def step():
         sim.run(sim.time + t_step)
 
     for _ in range(args.warmup):
+        reset()
         step()
     torch.cuda.synchronize()
     if world > 1:
@@ -457,6 +482,7 @@ def run_ours(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     for k in range(args.steps):
+        reset()  # outside the events, like the L2 flush
         flush.zero_()
         ev[k][0].record(stream)
         step()
@@ -475,7 +501,6 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers
     # pinned host buffers (page-locked, so the copies run at full DMA speed)
-    host_in = torch.from_numpy(np.ascontiguousarray(w.counts, np.int32)).pin_memory().numpy()
     host_out = torch.empty(host_in.shape, dtype=torch.int32).pin_memory().numpy()
     e2e_steps = max(3, min(args.steps, 10))
     t_e = []
@@ -511,6 +536,7 @@ def run_ours(args):
                    "windows_per_step": windows / args.steps, "form": "plain",
                    "kernel": "specialised" if sim.specialized else "generic",
                    "l2": "flushed before each timed step (256 MiB write, outside the events)",
+                   "step": "steps_run over sim_ms_per_step from the initial counts (reset outside the events)",
                    "parallelism": f"replicas{world}"},
         "e2e": e2e,
         "gpu_launches": int(l1 - l0),
@@ -554,8 +580,8 @@ def main():
                          "1.03M-tet dendrite")
     ap.add_argument("--sim-ms", type=float, default=0.0,
                     help="simulated ms per step of the headline workload (default: its t_end)")
-    ap.add_argument("--dendrite-ms", type=float, default=1.0,
-                    help="simulated ms per step of the dendrite measurement (0 = skip)")
+    ap.add_argument("--dendrite-ms", type=float, default=50.0,
+                    help="simulated ms per step of the dendrite measurement, from its initial counts (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
