@@ -211,6 +211,23 @@ def test_region_mask_and_zero_order_influx_bit_exact(capi):
     assert np.array_equal(gc, oc)
 
 
+def test_cuboid_equals_stored_oracle_values(capi):
+    """The CUDA path on the cuboid (A + B <-> C, 1,920 tets, 10 ms) against the
+    oracle's stored kernel-precision result in tests/golden/."""
+    import importlib.util
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "golden", "make_golden.py"))
+    golden = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(golden)
+    ref = golden.read(os.path.join(here, "golden", "cuboid_prec32.txt"))
+    w = I.config1()
+    g = capi.from_workload(w)
+    g.run(w.t_end)
+    assert g.windows == ref["windows"] and g.tau == ref["tau"]
+    assert np.array_equal(g.get_counts(), ref["counts"])
+
+
 def test_resume_on_window_grid_equals_single_run(capi):
     w = I.config2(nx=4, t_end=3e-3)
     a = capi.from_workload(w)
