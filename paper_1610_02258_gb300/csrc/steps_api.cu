@@ -1095,21 +1095,28 @@ int steps_batch_run(steps_batch *b, const double *t_end) {
         // time 3 windows at each candidate block size, keep the fastest
         const int cand[3] = {128, 256, 512};
         b->tune_ms.assign(3, 0.f);
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (!cuda_ok(cudaEventCreate(&e0), "steps_batch_run: autotuner event") ||
+            !cuda_ok(cudaEventCreate(&e1), "steps_batch_run: autotuner event")) {
+            if (e0) cudaEventDestroy(e0);
+            return STEPS_ERR_CUDA;
+        }
         float best = 1e30f;
         int best_b = b->block;
         for (int c = 0; c < 3 && rc == STEPS_OK; ++c) {
             rc = b->build_work(cand[c]);
             if (rc) break;
             rc = b->run_windows(cand[c], 1);  // warm
-            cudaEventRecord(e0, b->stream);
-            if (!rc) rc = b->run_windows(cand[c], 3);
-            cudaEventRecord(e1, b->stream);
-            cudaEventSynchronize(e1);
+            if (rc) break;
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            if (!cuda_ok(cudaEventRecord(e0, b->stream), "steps_batch_run: autotuner") ||
+                (rc = b->run_windows(cand[c], 3)) != STEPS_OK ||
+                !cuda_ok(cudaEventRecord(e1, b->stream), "steps_batch_run: autotuner") ||
+                !cuda_ok(cudaEventSynchronize(e1), "steps_batch_run: autotuner") ||
+                !cuda_ok(cudaEventElapsedTime(&ms, e0, e1), "steps_batch_run: autotuner")) {
+                if (rc == STEPS_OK) rc = STEPS_ERR_CUDA;
+                break;
+            }
             b->tune_ms[c] = ms / 3.f;
             if (ms < best) {
                 best = ms;
