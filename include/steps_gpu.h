@@ -369,6 +369,14 @@ const char *steps_last_error(void);
 int steps_debug_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out);
 /* The step kernel's float natural logarithm on the device, n values. */
 int steps_debug_logf(const float *x, int64_t n, float *out);
+/* The host-side set-up of steps_sim_create alone, with no device work (for
+ * tests of the host logic without a GPU): *tau (§2.1), the cumulative face
+ * thresholds of every tet at the full window ([nt*4] uint32, 2^31 fixed
+ * point, caller's tet order) and, if perm is not NULL, the internal tet order
+ * ([nt] int32: device index -> caller's tet id). reorder: STEPS_REORDER_*.
+ * Errors: STEPS_ERR_ARG (NULL mesh, model, tau or thr; bad reorder). */
+int steps_debug_host_tables(const steps_mesh *mesh, const steps_model *model, int32_t reorder, double *tau,
+                            uint32_t *thr, int32_t *perm);
 
 #ifdef __cplusplus
 }

@@ -34,6 +34,7 @@ EXPORTS = [
     "steps_sim_specialized", "steps_batch_specialized", "steps_sim_shape",
     "steps_server_options_default", "steps_server_create", "steps_server_destroy", "steps_server_submit",
     "steps_server_step", "steps_server_job_state", "steps_server_take_result", "steps_server_stats",
+    "steps_debug_host_tables",
 ]
 
 
@@ -98,6 +99,7 @@ def _load():
         "steps_sim_specialized": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
         "steps_batch_specialized": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
         "steps_sim_shape": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+        "steps_debug_host_tables": (ctypes.c_int, [P, P, i32, ctypes.POINTER(ctypes.c_double), P, P]),
         "steps_server_options_default": (None, [ctypes.POINTER(steps_server_options)]),
         "steps_server_create": (ctypes.c_int, [ctypes.POINTER(steps_server_options), P, PP]),
         "steps_server_destroy": (None, [P]),
@@ -282,6 +284,15 @@ def steps_debug_philox(seed, ctr):
     out = np.empty_like(c)
     _check(lib.steps_debug_philox(ctypes.c_uint64(seed), _ptr(c), c.shape[0], _ptr(out)))
     return out
+
+
+def steps_debug_host_tables(mesh, model, nt, reorder=STEPS_REORDER_MORTON):
+    """(tau, thresholds [nt, 4] in the caller's tet order, device order perm)."""
+    tau = ctypes.c_double()
+    thr = np.empty((nt, 4), np.uint32)
+    perm = np.empty(nt, np.int32)
+    _check(lib.steps_debug_host_tables(mesh, model, int(reorder), ctypes.byref(tau), _ptr(thr), _ptr(perm)))
+    return tau.value, thr, perm
 
 
 def steps_debug_logf(x):

@@ -810,6 +810,31 @@ int steps_debug_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *
     return rc;
 }
 
+int steps_debug_host_tables(const steps_mesh *mesh, const steps_model *model, int32_t reorder, double *tau,
+                            uint32_t *thr, int32_t *perm) {
+    CHECK_NULL(mesh, "steps_debug_host_tables");
+    CHECK_NULL(model, "steps_debug_host_tables");
+    CHECK_NULL(tau, "steps_debug_host_tables");
+    CHECK_NULL(thr, "steps_debug_host_tables");
+    if (reorder != STEPS_REORDER_NONE && reorder != STEPS_REORDER_MORTON) {
+        set_error("steps_debug_host_tables: bad reorder");
+        return STEPS_ERR_ARG;
+    }
+    Tables t;
+    try {
+        build_tables(mesh->m, model->m, reorder, t);
+    } catch (const std::bad_alloc &) {
+        set_error("steps_debug_host_tables: out of host memory");
+        return STEPS_ERR_OOM;
+    }
+    *tau = t.tau;
+    const size_t nt = t.perm.size();
+    for (size_t d = 0; d < nt; ++d)
+        for (int f = 0; f < 4; ++f) thr[(size_t)t.perm[d] * 4 + f] = t.thr_dev[d * 4 + f];
+    if (perm) std::memcpy(perm, t.perm.data(), nt * sizeof(int32_t));
+    return STEPS_OK;
+}
+
 int steps_debug_logf(const float *x, int64_t n, float *out) {
     CHECK_NULL(x, "steps_debug_logf");
     CHECK_NULL(out, "steps_debug_logf");

@@ -114,3 +114,46 @@ def test_server_host_side_arguments(capi):
         h2 = ctypes.c_void_p()
         assert lib.steps_server_create(ctypes.byref(b), None, ctypes.byref(h2)) == -1, field
     assert lib.steps_server_create(None, None, None) == -1
+
+
+@pytest.mark.parametrize("case", ["cuboid", "box", "dendrite", "shuffled"])
+def test_host_tables_equal_the_oracle(capi, case):
+    """The library's host set-up (geometry, tau, fixed-point face thresholds;
+    no device work) against the oracle's own: tau and every threshold equal
+    bit for bit, and the internal tet order is a permutation that does not
+    change them. Morton order brings face neighbours closer in memory."""
+    import oracle
+    if case == "cuboid":
+        w = I.config1()
+    elif case == "box":
+        w = I.config2(nx=5)
+    elif case == "dendrite":
+        w = I.config3(h=0.45e-6)
+    else:  # the cuboid with its tets listed in a random order
+        w = I.config1()
+        order = np.random.default_rng(2).permutation(w.n_tets)
+        w.tets = w.tets[order]
+        w.counts = w.counts[:, order]
+    mesh = capi.steps_mesh_create(w.verts, w.tets)
+    model = capi.steps_model_create(w.model.diff, w.model.lhs, w.model.rhs, w.model.k)
+    try:
+        tau, thr, perm = capi.steps_debug_host_tables(mesh, model, w.n_tets)
+        tau0, thr0, perm0 = capi.steps_debug_host_tables(mesh, model, w.n_tets, reorder=capi.STEPS_REORDER_NONE)
+    finally:
+        capi.steps_model_destroy(model)
+        capi.steps_mesh_destroy(mesh)
+    o = oracle.OracleSim(w.verts, w.tets, w.model, seed=1)
+    assert tau == tau0 == o.tau
+    assert np.array_equal(thr, o.thresholds()) and np.array_equal(thr0, thr)
+    assert np.array_equal(np.sort(perm), np.arange(w.n_tets)) and np.array_equal(perm0, np.arange(w.n_tets))
+    # face neighbours' distance in memory, caller's order vs Morton order
+    nbr, *_ = oracle.geometry(w.verts, w.tets)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(w.n_tets)
+    i, f = np.nonzero(nbr >= 0)
+    d_orig = np.abs(nbr[i, f] - i).mean()
+    d_morton = np.abs(inv[nbr[i, f]] - inv[i]).mean()
+    if case == "shuffled":
+        assert d_morton < 0.1 * d_orig
+    else:
+        assert d_morton < 2.0 * d_orig
