@@ -146,8 +146,14 @@ def test_host_tables_equal_the_oracle(capi, case):
     assert tau == tau0 == o.tau
     assert np.array_equal(thr, o.thresholds()) and np.array_equal(thr0, thr)
     assert np.array_equal(np.sort(perm), np.arange(w.n_tets)) and np.array_equal(perm0, np.arange(w.n_tets))
-    # face neighbours' distance in memory, caller's order vs Morton order
+    # cumulative per face, at most 2^31, and empty for boundary faces: a draw
+    # can never select a face without a neighbour (the kernel indexes nxt by it)
     nbr, *_ = oracle.geometry(w.verts, w.tets)
+    prev = np.concatenate([np.zeros((w.n_tets, 1), np.uint32), thr[:, :3]], axis=1)
+    assert np.all(thr >= prev) and int(thr.max()) <= 2**31
+    assert np.array_equal(thr[nbr < 0], prev[nbr < 0])
+    assert (nbr < 0).any()
+    # face neighbours' distance in memory, caller's order vs Morton order
     inv = np.empty_like(perm)
     inv[perm] = np.arange(w.n_tets)
     i, f = np.nonzero(nbr >= 0)
