@@ -133,3 +133,33 @@ def test_bad_meshes_rejected():
     oob[0, 0] = 999
     with pytest.raises(ValueError):
         oracle.OracleSim(verts, oob, m, seed=1)
+
+
+def test_full_box_jitter_bounds_and_volumes():
+    """The benchmark box mesh (294,780 tets, vertices jittered by up to 20 % of
+    the spacing h per axis): every vertex moves at most 0.2 h per axis,
+    boundary vertices stay in their boundary planes, no tet inverts, and the
+    smallest volume stays well above zero (the reading taken for the jitter:
+    at 0.2 h a Kuhn tet cannot invert, so nothing is resampled)."""
+    from paper_1610_02258_gb300 import inputs as I
+    h = 10.0 / 17.0 * I.UM
+    v0, tets = I.kuhn_box_mesh(170, 17, 17, h)
+    w = I.config2()
+    v = w.verts
+    assert v.shape == v0.shape and np.array_equal(w.tets, tets)
+    d = np.abs(v - v0)
+    assert d.max() <= 0.2 * h * (1 + 1e-12)
+    lo, hi = v0.min(axis=0), v0.max(axis=0)
+    on_face = (np.isclose(v0, lo, rtol=0, atol=1e-3 * h) | np.isclose(v0, hi, rtol=0, atol=1e-3 * h))
+    assert np.array_equal(v[on_face], v0[on_face])
+    def signed_volume(x):
+        p = x[tets]
+        return np.einsum("ij,ij->i", p[:, 1] - p[:, 0], np.cross(p[:, 2] - p[:, 0], p[:, 3] - p[:, 0])) / 6.0
+
+    vol, vol0 = signed_volume(v), signed_volume(v0)
+    nominal = h ** 3 / 6.0
+    assert np.allclose(np.abs(vol0), nominal, rtol=1e-9)
+    assert np.all(np.sign(vol) == np.sign(vol0))  # no tet turned inside out
+    assert np.abs(vol).min() > 0.1 * nominal
+    _, vol_o, *_ = oracle.geometry(v, tets)
+    assert np.allclose(vol_o, np.abs(vol), rtol=1e-9, atol=0)
