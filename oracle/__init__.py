@@ -54,6 +54,8 @@ def lib():
         L.orc_get_windows.restype = c_u64
         L.orc_get_thresholds.argtypes = [P, P]
         L.orc_get_cumg.argtypes = [P, P]
+        L.orc_get_species_thresholds.argtypes = [P, ctypes.c_int, ctypes.c_double, P]
+        L.orc_get_species_thresholds.restype = c_u32
         L.orc_geometry.argtypes = [c_i64, P, c_i64, P, P, P, P, P, P]
         L.orc_geometry.restype = ctypes.c_int
         L.orc_adjacency.argtypes = [c_i64, c_i64, P, P]
@@ -211,6 +213,13 @@ class OracleSim:
         out = np.empty((self.nt, 4))
         lib().orc_get_cumg(self._h, _p(out))
         return out
+
+    def species_thresholds(self, species: int, tau_k: float):
+        """(T [nt, 4] cumulative face thresholds, R_S species scale) that a
+        window of length tau_k uses for one species."""
+        out = np.empty((self.nt, 4), np.uint32)
+        scale = lib().orc_get_species_thresholds(self._h, int(species), float(tau_k), _p(out))
+        return out, int(scale)
 
 
 def from_workload(w, occ: int = OCC, prec: int = 64, seed=None) -> OracleSim:

@@ -554,6 +554,23 @@ static uint32_t species_scale(const orc_sim *s, int sp, double tau_k)
     return (uint32_t)fl;
 }
 
+/* Cumulative face thresholds of species sp in tet i for a window whose
+ * species scale is `scale`: T_f = (A_{i,f} * R_S) >> 31. */
+static void species_thresholds(const orc_sim *s, int64_t i, uint32_t scale, uint32_t T[4])
+{
+    for (int f = 0; f < 4; ++f)
+        T[f] = (uint32_t)(((uint64_t)s->thr[4 * i + f] * (uint64_t)scale) >> 31);
+}
+
+/* The thresholds every tet uses for species sp in a window of length tau_k
+ * ([nt*4]), and the species scale R_S as the return value. */
+uint32_t orc_get_species_thresholds(const orc_sim *s, int sp, double tau_k, uint32_t *out)
+{
+    uint32_t scale = species_scale(s, sp, tau_k);
+    for (int64_t i = 0; i < s->nt; ++i) species_thresholds(s, i, scale, out + 4 * i);
+    return scale;
+}
+
 /* One diffusion window of length tau_k over all tets (Algorithm 1). */
 static void window(orc_sim *s, double tau_k)
 {
@@ -575,8 +592,7 @@ static void window(orc_sim *s, double tau_k)
             int32_t leave[4] = {0, 0, 0, 0};
             if (s->D[sp] > 0.0) {
                 uint32_t T[4];
-                for (int f = 0; f < 4; ++f)
-                    T[f] = (uint32_t)(((uint64_t)s->thr[4 * i + f] * (uint64_t)scale[sp]) >> 31);
+                species_thresholds(s, i, scale[sp], T);
                 w += orc_sample_faces(s->seed, s->k_total, (uint32_t)i, w, M[sp], T, leave);
             }
             int32_t n = leave[0] + leave[1] + leave[2] + leave[3];
