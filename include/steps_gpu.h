@@ -40,7 +40,9 @@ extern "C" {
 #define STEPS_ERR_MODEL (-3)   /* invalid model (order > 2, negative rate, too many species) */
 #define STEPS_ERR_OOM (-4)     /* device or host allocation failed */
 #define STEPS_ERR_CUDA (-5)    /* a CUDA call failed */
-#define STEPS_ERR_TIMEOUT (-6) /* a bounded device wait ran out (the window's results are not valid) */
+#define STEPS_ERR_TIMEOUT (-6) /* a bounded device wait ran out: the window's results are not valid, and a bulk
+                                  copy may still be in flight, so the simulation (every member, for a batch) is
+                                  closed: later runs return STEPS_ERR_STATE until it is destroyed and rebuilt */
 #define STEPS_ERR_STATE (-7)   /* device-side check failed (negative count) or bad call order */
 
 #define STEPS_MAX_SPECIES 32
@@ -347,14 +349,18 @@ int steps_server_stats(const steps_server *srv, uint64_t *rounds, uint64_t *rebu
  * neither read nor written, so do not mix this call with steps_run on one
  * simulation without setting the counts again.
  * Scratch: a fixed device array in the library, two count buffers of at most
- * 4,194,304 int32 each (n_species * nt rounded up to a multiple of 32) plus an
- * error word: 32 MiB held on every GPU that loads the library until exit.
+ * 4,194,304 int32 each (n_species * (nt rounded up to a multiple of 32)) plus
+ * two error words: 32 MiB held on every GPU that loads the library until exit.
  * Larger problems get STEPS_ERR_ARG. The array is shared by every call and
  * keeps the last call's contents (each call clears it first); calls that
- * overlap on the GPU, on any stream or thread, race on it. The first call on
- * a device looks up the array's address with that device current; make that
- * first call before any stream capture. Synchronises with the simulation's
- * stream before returning. Errors as steps_run.
+ * overlap on the GPU, on any stream or thread, race on it. The device the
+ * simulation was created on must be current (else STEPS_ERR_ARG). The first
+ * call on a device looks up the array's address with that device current;
+ * make that first call before any stream capture. Synchronises with the
+ * simulation's stream before returning.
+ * Errors: d_counts holding a negative count gives STEPS_ERR_ARG before
+ * anything changes (clock and d_counts as before the call); otherwise as
+ * steps_run.
  */
 int steps_run_noalloc(steps_sim *sim, int32_t *d_counts, double t_end);
 

@@ -74,6 +74,8 @@ struct steps_sim {
     Tables tab;
     steps_options opt{};
     cudaStream_t stream = nullptr;
+    int device = -1;                // the device current at creation (owns every buffer below)
+    bool failed = false;            // a bounded device wait ran out: later runs are refused
     int64_t T = 0;
     int64_t Tpad = 0;
     int S = 0;
@@ -335,6 +337,7 @@ int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t 
     }
     s->model = model->m;
     s->stream = (cudaStream_t)cuda_stream;
+    if (!cuda_ok(cudaGetDevice(&s->device), "steps_sim_create: cudaGetDevice")) return STEPS_ERR_CUDA;
     s->T = mesh->m.nt;
     s->Tpad = (s->T + 31) / 32 * 32;
     s->S = s->model.S;
@@ -421,6 +424,7 @@ int steps_sim_clone(const steps_sim *src, uint64_t seed, void *cuda_stream, step
     s->tab = src->tab;
     s->opt = src->opt;
     s->stream = (cudaStream_t)cuda_stream;
+    s->device = src->device;
     s->T = src->T;
     s->Tpad = src->Tpad;
     s->S = src->S;
@@ -595,6 +599,15 @@ int steps_set_reac_mask(steps_sim *sim, int32_t reac, const uint8_t *active) {
 
 namespace {
 
+// A simulation whose bounded wait ran out stays closed: the block that gave up
+// may have left a bulk copy in flight, so its results cannot be trusted.
+int refuse_failed(const steps_sim *sim, const char *who) {
+    if (!sim->failed) return STEPS_OK;
+    set_error(std::string(who) + ": an earlier run of this simulation timed out on the device; "
+                                 "destroy it and create a new one");
+    return STEPS_ERR_STATE;
+}
+
 // Enqueues the windows of Algorithm 1 from the simulation's time to t_end
 // (full windows of tau, then a shortened last window); no synchronisation.
 int enqueue_run(steps_sim *sim, double t_end) {
@@ -637,7 +650,9 @@ int finish_run(steps_sim *sim, const char *who) {
     if (err) {
         cudaMemsetAsync(sim->d_err, 0, 4, sim->stream);
         if (err & 4u) {
-            set_error(std::string(who) + ": a bulk copy into shared memory did not complete within its wait limit");
+            sim->failed = true;
+            set_error(std::string(who) + ": a bulk copy into shared memory did not complete within its wait limit; "
+                                         "a copy may still be in flight, so this simulation is closed to further runs");
             return STEPS_ERR_TIMEOUT;
         }
         set_error(std::string(who) + (err & 2u ? ": a tet fired more than 2^24 reactions in one window (rates too large)"
@@ -667,6 +682,7 @@ int steps_run(steps_sim *sim, double t_end) {
         set_error("steps_run: t_end must be finite");
         return STEPS_ERR_ARG;
     }
+    if (int rf = refuse_failed(sim, "steps_run")) return rf;
     int rc = enqueue_run(sim, t_end);
     return rc ? rc : finish_run(sim, "steps_run");
 }
@@ -698,6 +714,7 @@ int steps_run_record(steps_sim *sim, double t_end, double dt_rec, int32_t n_spec
         set_error("steps_run_record: t_end must be finite and dt_rec finite and > 0");
         return STEPS_ERR_ARG;
     }
+    if (int rf = refuse_failed(sim, "steps_run_record")) return rf;
     if (n_species < 1 || n_species > sim->S || n_tets < 1 || max_records < 0) {
         set_error("steps_run_record: bad species or tet count");
         return STEPS_ERR_ARG;
@@ -1071,6 +1088,8 @@ int steps_batch_run(steps_batch *b, const double *t_end) {
             set_error("steps_batch_run: t_end must be finite");
             return STEPS_ERR_ARG;
         }
+    for (steps_sim *m : b->members)
+        if (int rf = refuse_failed(m, "steps_batch_run")) return rf;
     // members' own streams may still hold work
     for (steps_sim *m : b->members)
         if (!cuda_ok(cudaStreamSynchronize(m->stream), "steps_batch_run: member stream")) return STEPS_ERR_CUDA;
@@ -1204,7 +1223,9 @@ int steps_batch_run(steps_batch *b, const double *t_end) {
     if (err) {
         cudaMemset(b->d_err, 0, 4);
         if (err & 4u) {
-            set_error("steps_batch_run: a bulk copy into shared memory did not complete within its wait limit");
+            for (steps_sim *m : b->members) m->failed = true;
+            set_error("steps_batch_run: a bulk copy into shared memory did not complete within its wait limit; "
+                      "a copy may still be in flight, so every member is closed to further runs");
             return STEPS_ERR_TIMEOUT;
         }
         set_error(err & 2u ? "steps_batch_run: a tet fired more than 2^24 reactions in one window"
@@ -1242,15 +1263,15 @@ int steps_batch_info(const steps_batch *b, int32_t *block, uint64_t *launches, f
 // address; the address is looked up once per device with
 // cudaGetSymbolAddress, with that device current.
 // ---------------------------------------------------------------------------
-namespace {
-
 constexpr size_t kNoAllocMaxCounts = (size_t)1 << 22;  // n_species * Tpad per buffer
-__device__ __align__(256) int32_t g_noalloc_scratch[2 * kNoAllocMaxCounts + 64];
+static __device__ __align__(256) int32_t g_noalloc_scratch[2 * kNoAllocMaxCounts + 64];
+
+namespace {
 
 struct NoAllocScratch {
     bool ready = false;
     int32_t *counts = nullptr;  // [2][kNoAllocMaxCounts]
-    uint32_t *err = nullptr;    // one word after the count buffers
+    uint32_t *err = nullptr;    // two words after the count buffers: window error word, input check flag
 };
 
 constexpr int kNoAllocMaxDevices = 64;
@@ -1294,17 +1315,42 @@ extern "C" int steps_run_noalloc(steps_sim *sim, int32_t *d_counts, double t_end
                   " counts; use steps_run");
         return STEPS_ERR_ARG;
     }
+    if (int rf = refuse_failed(sim, "steps_run_noalloc")) return rf;
+    // the scratch address is per device, and the simulation's stream and
+    // tables belong to the device it was created on
+    int dev = -1;
+    if (!cuda_ok(cudaGetDevice(&dev), "steps_run_noalloc: cudaGetDevice")) return STEPS_ERR_CUDA;
+    if (dev != sim->device) {
+        set_error("steps_run_noalloc: the current device (" + std::to_string(dev) +
+                  ") is not the one the simulation was created on (" + std::to_string(sim->device) +
+                  "); make that device current first");
+        return STEPS_ERR_ARG;
+    }
     NoAllocScratch sc;
     int rc = noalloc_scratch(sc);
     if (rc) return rc;
     int32_t *buf[2] = {sc.counts, sc.counts + kNoAllocMaxCounts};
     cudaStream_t st = sim->stream;
     // the scratch keeps the previous call's contents: clear both buffers
-    // (padding and receiving rows must be zero) and the error word
+    // (padding and receiving rows must be zero) and both error words
     if (!cuda_ok(cudaMemsetAsync(buf[0], 0, S * Tpad * 4, st), "steps_run_noalloc: clear") ||
         !cuda_ok(cudaMemsetAsync(buf[1], 0, S * Tpad * 4, st), "steps_run_noalloc: clear") ||
-        !cuda_ok(cudaMemsetAsync(sc.err, 0, 4, st), "steps_run_noalloc: clear"))
+        !cuda_ok(cudaMemsetAsync(sc.err, 0, 8, st), "steps_run_noalloc: clear"))
         return STEPS_ERR_CUDA;
+    // reject negative input counts before anything (clock, caller's buffer) changes
+    {
+        const int64_t n = (int64_t)(S * T);
+        uint32_t neg = 0;
+        any_negative<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(d_counts, n, sc.err + 1);
+        if (!cuda_ok(cudaGetLastError(), "steps_run_noalloc: check") ||
+            !cuda_ok(cudaMemcpyAsync(&neg, sc.err + 1, 4, cudaMemcpyDeviceToHost, st), "steps_run_noalloc: check") ||
+            !cuda_ok(cudaStreamSynchronize(st), "steps_run_noalloc: check"))
+            return STEPS_ERR_CUDA;
+        if (neg) {
+            set_error("steps_run_noalloc: negative count in d_counts");
+            return STEPS_ERR_ARG;
+        }
+    }
     const unsigned grid = (unsigned)((T + 255) / 256);
     scatter_to_device_order<<<grid, 256, 0, st>>>(d_counts, (int64_t)T, (int32_t)S, sim->d_inv_perm, buf[0], Tpad);
     if (!cuda_ok(cudaGetLastError(), "steps_run_noalloc: scatter")) return STEPS_ERR_CUDA;
@@ -1350,7 +1396,9 @@ extern "C" int steps_run_noalloc(steps_sim *sim, int32_t *d_counts, double t_end
         !cuda_ok(cudaStreamSynchronize(st), "steps_run_noalloc"))
         return STEPS_ERR_CUDA;
     if (err & 4u) {
-        set_error("steps_run_noalloc: a bulk copy into shared memory did not complete within its wait limit");
+        sim->failed = true;
+        set_error("steps_run_noalloc: a bulk copy into shared memory did not complete within its wait limit; "
+                  "a copy may still be in flight, so this simulation is closed to further runs");
         return STEPS_ERR_TIMEOUT;
     }
     if (err) {

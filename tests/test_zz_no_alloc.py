@@ -46,6 +46,31 @@ def test_noalloc_equals_steps_run_on_two_calls_in_a_row(capi, specialize):
         assert new.windows == ref.windows and new.time == ref.time
         assert np.array_equal(got, expect)  # integer counts: bit-exact, as every parity test here
     assert int(expect.sum()) > 0
+    # the simulation's own count buffers were neither read nor written
+    assert np.array_equal(new.get_counts(), w.counts)
+
+
+def test_noalloc_rejects_negative_counts_before_anything_changes(capi):
+    """A negative input count is an argument error: the clock and the
+    caller's buffer stay as they were, and a corrected buffer then runs."""
+    import torch
+    w = I.config2(nx=4, t_end=2e-3)
+    sim = capi.from_workload(w)
+    ref = capi.from_workload(w)
+    bad = np.ascontiguousarray(w.counts).copy()
+    bad[3, 17] = -1
+    d = torch.from_numpy(bad).to("cuda")
+    t_end = 3.5 * sim.tau
+    with pytest.raises(capi.StepsError) as e:
+        capi.steps_run_noalloc(sim._sim, d.data_ptr(), t_end)
+    assert e.value.code == -1 and "negative" in str(e.value)
+    assert sim.windows == 0 and sim.time == 0.0
+    assert np.array_equal(d.cpu().numpy(), bad)
+    d.copy_(torch.from_numpy(np.ascontiguousarray(w.counts)))
+    capi.steps_run_noalloc(sim._sim, d.data_ptr(), t_end)
+    ref.run(t_end)
+    assert sim.windows == ref.windows == 4
+    assert np.array_equal(d.cpu().numpy(), ref.get_counts())
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(capi):
@@ -57,4 +82,4 @@ def test_noalloc_rejects_problems_beyond_its_scratch(capi):
     with pytest.raises(capi.StepsError) as e:
         capi.steps_run_noalloc(sim._sim, d.data_ptr(), 1e-3)
     assert e.value.code == -1 and "exceeds the fixed scratch" in str(e.value)
-    assert sim.windows == 0
+    assert sim.windows == 0 and sim.time == 0.0
