@@ -44,6 +44,10 @@ def lib():
         L.orc_run.restype = ctypes.c_int
         L.orc_step.argtypes = [P, ctypes.c_double]
         L.orc_step.restype = ctypes.c_int
+        L.orc_run_threads.argtypes = [P, ctypes.c_double, ctypes.c_int]
+        L.orc_run_threads.restype = ctypes.c_int
+        L.orc_step_threads.argtypes = [P, ctypes.c_double, ctypes.c_int]
+        L.orc_step_threads.restype = ctypes.c_int
         L.orc_get_tau.argtypes = [P]
         L.orc_get_tau.restype = ctypes.c_double
         L.orc_get_time.argtypes = [P]
@@ -182,11 +186,21 @@ class OracleSim:
             out[s] = row
         return out
 
-    def run(self, t_end: float):
-        lib().orc_run(self._h, float(t_end))
+    def run(self, t_end: float, threads: int = 1):
+        """Advance to t_end. threads > 1 runs each window on that many host
+        threads (gather form); the result is the serial one, bit for bit."""
+        if threads > 1:
+            if lib().orc_run_threads(self._h, float(t_end), int(threads)) != 0:
+                raise ValueError("oracle: bad thread count or out of memory")
+        else:
+            lib().orc_run(self._h, float(t_end))
 
-    def step(self, tau_k: float):
-        lib().orc_step(self._h, float(tau_k))
+    def step(self, tau_k: float, threads: int = 1):
+        if threads > 1:
+            if lib().orc_step_threads(self._h, float(tau_k), int(threads)) != 0:
+                raise ValueError("oracle: bad thread count or out of memory")
+        else:
+            lib().orc_step(self._h, float(tau_k))
 
     @property
     def tau(self):

@@ -44,6 +44,8 @@
  *     a = k/(N_A V) N_X N_Y, homodimer a = k/(N_A V) N_X (N_X - 1).
  */
 #include <math.h>
+#include <pthread.h>
+#include <stdatomic.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -275,6 +277,9 @@ typedef struct {
     int64_t k_grid;
     uint64_t k_total;
     int64_t events;    /* reaction events fired so far */
+    /* threaded (gather-form) windows only */
+    int32_t *rev;      /* [nt*4] local face of the neighbour that points back, -1 on the boundary */
+    int32_t *mv;       /* [S*nt*4] molecules tet i sends through face f, species-major */
 } orc_sim;
 
 /* tau from §2.1 and the fixed-point thresholds of every tet's faces. */
@@ -311,6 +316,7 @@ void orc_destroy(orc_sim *s)
     if (!s) return;
     free(s->nbr); free(s->vol); free(s->g); free(s->cumg); free(s->thr);
     free(s->cnt); free(s->nxt); free(s->mask);
+    free(s->rev); free(s->mv);
     free(s);
 }
 
@@ -437,7 +443,8 @@ static float prop32(const orc_sim *s, int r, const int32_t *N, float inv_nav)
     }
 }
 
-static void reaction_phase(orc_sim *s, int64_t i, double tau_k, double inv_tau_k, int32_t *N, int32_t *M)
+static void reaction_phase(const orc_sim *s, int64_t i, double tau_k, double inv_tau_k, int32_t *N, int32_t *M,
+                           int64_t *events)
 {
     double nav = ORC_AVOGADRO * (s->vol[i] * 1000.0); /* molecules per mol/L */
     float inv_nav = (float)(1.0 / nav);
@@ -495,7 +502,7 @@ static void reaction_phase(orc_sim *s, int64_t i, double tau_k, double inv_tau_k
             touched[sp] = 1;
             N[sp] += delta;
         }
-        s->events++;
+        (*events)++;
     }
 
     /* Mean occupancy -> integer trial count (Algorithm 1: Nbar = O_S / tau). */
@@ -584,7 +591,7 @@ static void window(orc_sim *s, double tau_k)
     for (int64_t i = 0; i < nt; ++i) {
         for (int sp = 0; sp < S; ++sp) N[sp] = s->cnt[(size_t)sp * nt + i];
         /* reaction SSA operator */
-        reaction_phase(s, i, tau_k, inv_tau_k, N, M);
+        reaction_phase(s, i, tau_k, inv_tau_k, N, M, &s->events);
         /* diffusion operator: every diffusive species in species order draws
          * from one per-tet word stream */
         uint32_t w = 0;
@@ -626,6 +633,162 @@ int orc_run(orc_sim *s, double t_end)
         }
     }
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same window on several host threads (the CPU baseline's all-core     */
+/* figure). Jacobi in gather form: pass 1 runs every tet's reaction         */
+/* operator and leave draws independently (each tet's draws depend only on  */
+/* its own state and its own random stream) and records what it keeps and   */
+/* what it sends through each face; pass 2 adds to every tet what its face   */
+/* neighbours sent it. Integer sums, so the result is the serial window's,  */
+/* bit for bit, whatever the thread count or schedule.                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    orc_sim *s;
+    double tau_k, inv_tau_k;
+    const uint32_t *scale;
+    int pass;
+    atomic_llong next;     /* next chunk of tets to take */
+    atomic_llong events;
+} orc_par_job;
+
+enum { ORC_PAR_CHUNK = 256 };
+
+static void par_tet_pass1(orc_par_job *job, int64_t i, int64_t *events)
+{
+    orc_sim *s = job->s;
+    const int64_t nt = s->nt;
+    int32_t N[ORC_MAXS], M[ORC_MAXS];
+    for (int sp = 0; sp < s->S; ++sp) N[sp] = s->cnt[(size_t)sp * nt + i];
+    reaction_phase(s, i, job->tau_k, job->inv_tau_k, N, M, events);
+    uint32_t w = 0;
+    for (int sp = 0; sp < s->S; ++sp) {
+        int32_t leave[4] = {0, 0, 0, 0};
+        if (s->D[sp] > 0.0) {
+            uint32_t T[4];
+            species_thresholds(s, i, job->scale[sp], T);
+            w += orc_sample_faces(s->seed, s->k_total, (uint32_t)i, w, M[sp], T, leave);
+        }
+        int32_t n = leave[0] + leave[1] + leave[2] + leave[3];
+        s->nxt[(size_t)sp * nt + i] = N[sp] - n;
+        memcpy(s->mv + ((size_t)sp * nt + i) * 4, leave, sizeof(leave));
+    }
+}
+
+static void par_tet_pass2(orc_sim *s, int64_t i)
+{
+    const int64_t nt = s->nt;
+    for (int sp = 0; sp < s->S; ++sp) {
+        int32_t add = 0;
+        for (int f = 0; f < 4; ++f) {
+            int32_t j = s->nbr[4 * i + f];
+            if (j >= 0) add += s->mv[((size_t)sp * nt + j) * 4 + s->rev[4 * i + f]];
+        }
+        s->nxt[(size_t)sp * nt + i] += add;
+    }
+}
+
+static void *par_worker(void *arg)
+{
+    orc_par_job *job = (orc_par_job *)arg;
+    const int64_t nt = job->s->nt;
+    int64_t events = 0;
+    for (;;) {
+        int64_t i0 = (int64_t)atomic_fetch_add(&job->next, ORC_PAR_CHUNK);
+        if (i0 >= nt) break;
+        int64_t i1 = i0 + ORC_PAR_CHUNK < nt ? i0 + ORC_PAR_CHUNK : nt;
+        for (int64_t i = i0; i < i1; ++i) {
+            if (job->pass == 1) par_tet_pass1(job, i, &events);
+            else par_tet_pass2(job->s, i);
+        }
+    }
+    atomic_fetch_add(&job->events, (long long)events);
+    return NULL;
+}
+
+static int par_ensure(orc_sim *s)
+{
+    if (s->rev) return ORC_OK;
+    s->rev = (int32_t *)malloc(sizeof(int32_t) * 4 * s->nt);
+    s->mv = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)s->S * s->nt);
+    if (!s->rev || !s->mv) { free(s->rev); free(s->mv); s->rev = s->mv = NULL; return ORC_ERR_OOM; }
+    for (int64_t i = 0; i < s->nt; ++i)
+        for (int f = 0; f < 4; ++f) {
+            int32_t j = s->nbr[4 * i + f], back = -1;
+            if (j >= 0)
+                for (int g = 0; g < 4; ++g)
+                    if (s->nbr[4 * (int64_t)j + g] == (int32_t)i) back = g;
+            s->rev[4 * i + f] = back;
+        }
+    return ORC_OK;
+}
+
+static int par_pass(orc_par_job *job, int pass, int nthreads)
+{
+    pthread_t th[256];
+    int started = 0;
+    job->pass = pass;
+    atomic_store(&job->next, 0);
+    for (int k = 1; k < nthreads; ++k) {
+        if (pthread_create(&th[started], NULL, par_worker, job) != 0) break;
+        ++started;
+    }
+    par_worker(job); /* the calling thread works too */
+    for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
+    return ORC_OK;
+}
+
+static int window_threads(orc_sim *s, double tau_k, int nthreads)
+{
+    int rc = par_ensure(s);
+    if (rc) return rc;
+    uint32_t scale[ORC_MAXS];
+    for (int sp = 0; sp < s->S; ++sp) scale[sp] = species_scale(s, sp, tau_k);
+    orc_par_job job;
+    job.s = s;
+    job.tau_k = tau_k;
+    job.inv_tau_k = 1.0 / tau_k;
+    job.scale = scale;
+    atomic_init(&job.next, 0);
+    atomic_init(&job.events, 0);
+    par_pass(&job, 1, nthreads);
+    par_pass(&job, 2, nthreads);
+    s->events += (int64_t)atomic_load(&job.events);
+    int32_t *tmp = s->cnt; s->cnt = s->nxt; s->nxt = tmp;
+    s->k_total++;
+    return ORC_OK;
+}
+
+/* orc_run on `nthreads` host threads (1..256): the same windows, the same result. */
+int orc_run_threads(orc_sim *s, double t_end, int nthreads)
+{
+    if (nthreads < 1 || nthreads > 256) return ORC_ERR_ARG;
+    for (;;) {
+        double t = orc_get_time(s);
+        double tol = isfinite(s->tau) ? 1e-9 * s->tau : 0.0;
+        if (!(t_end - t > tol)) break;
+        int rc;
+        if (isfinite(s->tau) && t + s->tau <= t_end + tol) {
+            rc = window_threads(s, s->tau, nthreads);
+            if (rc) return rc;
+            s->k_grid++;
+        } else {
+            rc = window_threads(s, t_end - t, nthreads);
+            if (rc) return rc;
+            s->t_base = t_end;
+            s->k_grid = 0;
+            break;
+        }
+    }
+    return ORC_OK;
+}
+
+/* One window of explicit length on `nthreads` host threads. */
+int orc_step_threads(orc_sim *s, double tau_k, int nthreads)
+{
+    if (nthreads < 1 || nthreads > 256) return ORC_ERR_ARG;
+    return window_threads(s, tau_k, nthreads);
 }
 
 /* One window of explicit length (for tests of the operator on its own). */
