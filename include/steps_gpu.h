@@ -272,8 +272,13 @@ typedef struct steps_server_options {
     int32_t wave_windows;  /* windows of its own tau a job advances per round; default 16 */
     int32_t block;         /* threads per block of the batched kernel; default 256 (fixed: batches re-form
                               whenever jobs come and go, so no autotuning) */
-    int32_t specialize;    /* as steps_batch_options.specialize; default -1 (the generic batched kernel, no
-                              run-time compilation between requests) */
+    int32_t specialize;    /* -1 (default): all running jobs in one batch on the generic batched kernel.
+                              0 or 1: jobs grouped by model structure, one batch per group, the groups'
+                              batches running at the same time on streams the server creates; each
+                              batch takes steps_batch_options.specialize = this value (1: the kernel
+                              compiled for the group's model; create the prototypes with
+                              steps_options.specialize = 1 so that it is compiled then, once per model
+                              structure, and never between requests) */
     int32_t reserved[2];   /* set to 0 */
 } steps_server_options;
 
@@ -287,7 +292,8 @@ void steps_server_options_default(steps_server_options *opt);
  * runs). Because every random number is addressed by (job seed, window,
  * original tet), a job's result is the same bits as the same simulation run
  * alone with steps_run, whatever else runs beside it.
- * cuda_stream: stream of the server's launches (NULL = legacy default stream).
+ * cuda_stream: stream of the server's launches with specialize = -1, and of
+ * every job's set-up and result copies (NULL = legacy default stream).
  * Errors: STEPS_ERR_ARG (NULL, max_jobs < 1, wave_windows < 1, bad block).
  */
 int steps_server_create(const steps_server_options *opt, void *cuda_stream, steps_server **out);

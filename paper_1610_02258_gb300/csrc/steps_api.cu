@@ -886,6 +886,7 @@ struct steps_batch {
     RepEntry *h_reps = nullptr;  // pinned host mirror
     RepEntry *d_reps = nullptr;
     uint32_t *d_err = nullptr;
+    uint32_t *h_err = nullptr;   // pinned copy of the error word, read after the stream completes
     struct Work {
         BlockWork *d = nullptr;
         int64_t n = 0;
@@ -908,6 +909,7 @@ struct steps_batch {
         }
         cudaFree(d_reps);
         cudaFree(d_err);
+        cudaFreeHost(h_err);
         cudaFreeHost(h_reps);
     }
 
@@ -1042,6 +1044,7 @@ int steps_batch_create(steps_sim *const *members, int32_t n, const steps_batch_o
         b->any_order0 = b->any_order0 || members[j]->model.dev.order0 != 0u;
     }
     if (!cuda_ok(cudaMallocHost((void **)&b->h_reps, sizeof(RepEntry) * n), "steps_batch_create: host alloc") ||
+        !cuda_ok(cudaMallocHost((void **)&b->h_err, 4), "steps_batch_create: host alloc") ||
         !cuda_ok(cudaMalloc((void **)&b->d_reps, sizeof(RepEntry) * n), "steps_batch_create: alloc") ||
         !cuda_ok(cudaMalloc((void **)&b->d_err, 4), "steps_batch_create: alloc") ||
         !cuda_ok(cudaMemset(b->d_err, 0, 4), "steps_batch_create: memset"))
@@ -1079,7 +1082,14 @@ void steps_batch_destroy(steps_batch *b) {
     delete b;
 }
 
-int steps_batch_run(steps_batch *b, const double *t_end) {
+}  // extern "C"
+
+namespace steps {
+
+// steps_batch_run without its final wait: every window is enqueued on the
+// batch's stream, the members' clocks advanced and the error word's copy to
+// the host enqueued. batch_finish waits and turns the word into a code.
+int batch_enqueue(steps_batch *b, const double *t_end) {
     CHECK_NULL(b, "steps_batch_run");
     CHECK_NULL(t_end, "steps_batch_run");
     const size_t n = b->members.size();
@@ -1216,10 +1226,15 @@ int steps_batch_run(steps_batch *b, const double *t_end) {
             m->k_grid += nfull[j];
         }
     }
-    uint32_t err = 0;
-    if (!cuda_ok(cudaMemcpyAsync(&err, b->d_err, 4, cudaMemcpyDeviceToHost, b->stream), "steps_batch_run: error word") ||
-        !cuda_ok(cudaStreamSynchronize(b->stream), "steps_batch_run"))
+    if (!cuda_ok(cudaMemcpyAsync(b->h_err, b->d_err, 4, cudaMemcpyDeviceToHost, b->stream),
+                 "steps_batch_run: error word"))
         return STEPS_ERR_CUDA;
+    return STEPS_OK;
+}
+
+int batch_finish(steps_batch *b) {
+    if (!cuda_ok(cudaStreamSynchronize(b->stream), "steps_batch_run")) return STEPS_ERR_CUDA;
+    const uint32_t err = *b->h_err;
     if (err) {
         cudaMemset(b->d_err, 0, 4);
         if (err & 4u) {
@@ -1233,6 +1248,17 @@ int steps_batch_run(steps_batch *b, const double *t_end) {
         return STEPS_ERR_STATE;
     }
     return STEPS_OK;
+}
+
+std::string sim_structure_key(const steps_sim *sim) { return spec_program_source(sim->model, 256); }
+
+}  // namespace steps
+
+extern "C" {
+
+int steps_batch_run(steps_batch *b, const double *t_end) {
+    int rc = steps::batch_enqueue(b, t_end);
+    return rc ? rc : steps::batch_finish(b);
 }
 
 int steps_batch_specialized(const steps_batch *b, int32_t *specialized) {

@@ -75,4 +75,13 @@ std::string spec_program_source(const HostModel &hm, int block);
 // whether the specialised kernels keep the trial counts in StepArgs::trial
 bool spec_global_trial(const HostModel &hm);
 
+// steps_api.cu: steps_batch_run in two parts (enqueue every window and the
+// error word's copy; then wait and map the word to a return code), so that
+// batches on different streams can run at the same time; and a key that is
+// equal for simulations whose models share one structure (one specialised
+// kernel serves them all).
+int batch_enqueue(steps_batch *b, const double *t_end);
+int batch_finish(steps_batch *b);
+std::string sim_structure_key(const steps_sim *sim);
+
 }  // namespace steps

@@ -3,13 +3,16 @@
 // Host-side scheduling on top of the C ABI: jobs are clones of a prototype
 // simulation (steps_sim_clone), admitted first come first served while a slot
 // is free and their device memory fits the budget, and advanced together in
-// rounds. A round is one batched run (steps_batch_run) that moves every
-// running job by up to wave_windows windows of its own tau, stopping on its
+// rounds. A round is one batched run per group of running jobs that moves
+// every job by up to wave_windows windows of its own tau, stopping on its
 // window grid or at its t_end, so no extra shortened windows are inserted.
-// Finished jobs leave between rounds (counts copied to the host, device
-// memory freed); the batch is re-formed only when the set of running jobs
-// changed. Every draw is addressed by (job seed, window, tet), so a job's
-// result does not depend on what runs beside it.
+// With the generic kernel all running jobs form one group; otherwise jobs
+// are grouped by model structure, each group runs the step kernel compiled
+// for its model, and the groups' batches run at the same time on streams of
+// their own. Finished jobs leave between rounds (counts copied to the host,
+// device memory freed); a group's batch is re-formed only when its set of
+// running jobs changed. Every draw is addressed by (job seed, window, tet),
+// so a job's result does not depend on what runs beside it.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -17,6 +20,8 @@
 #include <new>
 #include <string>
 #include <vector>
+
+#include <cuda_runtime.h>
 
 #include "steps_internal.h"
 
@@ -34,6 +39,17 @@ struct Job {
     double t = 0.0;
 };
 
+// Running jobs that advance in one batched launch per window.
+struct Group {
+    std::string key;               // model structure ("" = every job, generic kernel)
+    std::vector<int64_t> running;  // job ids, in batch member order
+    steps_batch *batch = nullptr;  // over `running` when valid
+    bool valid = false;
+    cudaStream_t stream = nullptr; // the server's stream (one group) or one of the group's own
+    bool own_stream = false;
+    bool enqueued = false;
+};
+
 }  // namespace
 
 struct steps_server {
@@ -41,24 +57,27 @@ struct steps_server {
     void *stream = nullptr;
     std::vector<Job> jobs;
     std::deque<int64_t> queue;     // queued job ids, by submission
-    std::vector<int64_t> running;  // running job ids, in batch member order
-    steps_batch *batch = nullptr;  // over `running` when batch_valid
-    bool batch_valid = false;
+    std::vector<Group> groups;
+    std::vector<int> job_group;    // group index of every job
+    int32_t n_running = 0;
     uint64_t rounds = 0, rebuilds = 0, launches = 0;
     int64_t bytes_running = 0;
 
-    void drop_batch() {
-        if (batch) {
+    void drop_batch(Group &g) {
+        if (g.batch) {
             uint64_t l = 0;
-            if (steps_batch_info(batch, nullptr, &l, nullptr) == STEPS_OK) launches += l;
-            steps_batch_destroy(batch);
+            if (steps_batch_info(g.batch, nullptr, &l, nullptr) == STEPS_OK) launches += l;
+            steps_batch_destroy(g.batch);
         }
-        batch = nullptr;
-        batch_valid = false;
+        g.batch = nullptr;
+        g.valid = false;
     }
 
     ~steps_server() {
-        drop_batch();
+        for (Group &g : groups) {
+            drop_batch(g);
+            if (g.own_stream) cudaStreamDestroy(g.stream);
+        }
         for (Job &j : jobs)
             if (j.sim) steps_sim_destroy(j.sim);
     }
@@ -67,6 +86,36 @@ struct steps_server {
 namespace {
 
 bool valid_job(const steps_server *srv, int64_t job) { return job >= 0 && job < (int64_t)srv->jobs.size(); }
+
+// The group a job of this prototype runs in (created on first use).
+int group_of(steps_server *srv, const steps_sim *proto, int *out) {
+    const std::string key = srv->opt.specialize < 0 ? std::string() : steps::sim_structure_key(proto);
+    for (size_t g = 0; g < srv->groups.size(); ++g)
+        if (srv->groups[g].key == key) {
+            *out = (int)g;
+            return STEPS_OK;
+        }
+    Group g;
+    g.key = key;
+    if (srv->opt.specialize < 0) {
+        g.stream = (cudaStream_t)srv->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            steps::set_error("steps_server_submit: cudaStreamCreateWithFlags failed");
+            return STEPS_ERR_CUDA;
+        }
+        g.own_stream = true;
+    }
+    try {
+        srv->groups.push_back(std::move(g));
+    } catch (const std::bad_alloc &) {
+        steps::set_error("steps_server_submit: out of host memory");
+        return STEPS_ERR_OOM;
+    }
+    *out = (int)srv->groups.size() - 1;
+    return STEPS_OK;
+}
 
 // Clone the prototype, set its counts: the job is running.
 int admit(steps_server *srv, int64_t id) {
@@ -84,9 +133,11 @@ int admit(steps_server *srv, int64_t id) {
     j.state = 1;
     j.counts.clear();
     j.counts.shrink_to_fit();
-    srv->running.push_back(id);
+    Group &g = srv->groups[(size_t)srv->job_group[(size_t)id]];
+    g.running.push_back(id);
+    g.valid = false;
+    srv->n_running += 1;
     srv->bytes_running += j.bytes;
-    srv->batch_valid = false;
     return STEPS_OK;
 }
 
@@ -111,6 +162,7 @@ int retire(steps_server *srv, int64_t id) {
     j.sim = nullptr;
     j.state = 2;
     srv->bytes_running -= j.bytes;
+    srv->n_running -= 1;
     j.bytes = 0;
     return STEPS_OK;
 }
@@ -173,6 +225,9 @@ int steps_server_submit(steps_server *srv, const steps_sim *proto, uint64_t seed
     int32_t ns = 0;
     int rc = steps_sim_shape(proto, &nt, &ns);
     if (rc) return rc;
+    int grp = 0;
+    rc = group_of(srv, proto, &grp);
+    if (rc) return rc;
     Job j;
     j.proto = proto;
     j.seed = seed;
@@ -180,6 +235,7 @@ int steps_server_submit(steps_server *srv, const steps_sim *proto, uint64_t seed
     try {
         j.counts.assign(counts, counts + (size_t)ns * (size_t)nt);
         srv->jobs.push_back(std::move(j));
+        srv->job_group.push_back(grp);
         srv->queue.push_back((int64_t)srv->jobs.size() - 1);
     } catch (const std::bad_alloc &) {
         steps::set_error("steps_server_submit: out of host memory");
@@ -196,50 +252,68 @@ int steps_server_step(steps_server *srv, int32_t *running, int32_t *finished) {
     }
     int32_t nfin = 0;
     // admission: first come first served, by slots and device-memory budget
-    while (!srv->queue.empty() && (int32_t)srv->running.size() < srv->opt.max_jobs) {
+    while (!srv->queue.empty() && srv->n_running < srv->opt.max_jobs) {
         const int64_t id = srv->queue.front();
         int64_t need = 0;
         int rc = steps_sim_device_bytes(srv->jobs[(size_t)id].proto, &need);
         if (rc) return rc;
-        if (!srv->running.empty() && srv->opt.device_budget > 0 && srv->bytes_running + need > srv->opt.device_budget)
+        if (srv->n_running > 0 && srv->opt.device_budget > 0 && srv->bytes_running + need > srv->opt.device_budget)
             break;
         rc = admit(srv, id);
         if (rc) return rc;
         srv->queue.pop_front();
     }
-    // jobs with nothing to run (t_end 0) finish at once
-    std::vector<int64_t> keep;
-    for (int64_t id : srv->running) {
-        Job &j = srv->jobs[(size_t)id];
-        double t = 0.0;
-        steps_get_time(j.sim, &t);
-        if (!(t < j.t_end - 1e-12 * std::max(j.t_end, 1e-30))) {
-            int rc = retire(srv, id);
-            if (rc) return rc;
-            ++nfin;
-            srv->batch_valid = false;
-        } else {
-            keep.push_back(id);
+    // jobs at their t_end (nothing to run, or finished last round) leave
+    auto sweep = [&](Group &g) -> int {
+        std::vector<int64_t> keep;
+        for (int64_t id : g.running) {
+            Job &j = srv->jobs[(size_t)id];
+            double t = 0.0;
+            steps_get_time(j.sim, &t);
+            steps_get_windows(j.sim, &j.windows, nullptr);
+            j.t = t;
+            if (!(t < j.t_end - 1e-12 * std::max(j.t_end, 1e-30))) {
+                int rc = retire(srv, id);
+                if (rc) return rc;
+                ++nfin;
+                g.valid = false;
+            } else {
+                keep.push_back(id);
+            }
         }
+        g.running.swap(keep);
+        if (!g.valid) srv->drop_batch(g);
+        return STEPS_OK;
+    };
+    for (Group &g : srv->groups) {
+        int rc = sweep(g);
+        if (rc) return rc;
     }
-    srv->running.swap(keep);
-    if (!srv->running.empty()) {
-        if (!srv->batch_valid) {
-            srv->drop_batch();
+    // one round: every group's batch moves its jobs by up to wave_windows
+    // windows on their own grids; the groups' streams run at the same time
+    bool any = false;
+    int rc_first = STEPS_OK;
+    for (Group &g : srv->groups) {
+        g.enqueued = false;
+        if (g.running.empty()) continue;
+        if (!g.valid) {
+            srv->drop_batch(g);
             std::vector<steps_sim *> members;
-            for (int64_t id : srv->running) members.push_back(srv->jobs[(size_t)id].sim);
+            for (int64_t id : g.running) members.push_back(srv->jobs[(size_t)id].sim);
             steps_batch_options bo;
             steps_batch_options_default(&bo);
             bo.block = srv->opt.block;
             bo.specialize = srv->opt.specialize;
-            int rc = steps_batch_create(members.data(), (int32_t)members.size(), &bo, srv->stream, &srv->batch);
-            if (rc) return rc;
-            srv->batch_valid = true;
+            int rc = steps_batch_create(members.data(), (int32_t)members.size(), &bo, g.stream, &g.batch);
+            if (rc) {
+                rc_first = rc;
+                break;
+            }
+            g.valid = true;
             ++srv->rebuilds;
         }
-        // one round: every job by up to wave_windows windows on its own grid
         std::vector<double> target;
-        for (int64_t id : srv->running) {
+        for (int64_t id : g.running) {
             Job &j = srv->jobs[(size_t)id];
             double t = 0.0, tau = 0.0;
             steps_get_time(j.sim, &t);
@@ -247,30 +321,28 @@ int steps_server_step(steps_server *srv, int32_t *running, int32_t *finished) {
             const double tg = std::isfinite(tau) ? t + (double)srv->opt.wave_windows * tau : j.t_end;
             target.push_back(std::min(j.t_end, tg));
         }
-        int rc = steps_batch_run(srv->batch, target.data());
-        if (rc) return rc;
-        ++srv->rounds;
-        // retire the jobs that reached t_end
-        keep.clear();
-        for (int64_t id : srv->running) {
-            Job &j = srv->jobs[(size_t)id];
-            double t = 0.0;
-            steps_get_time(j.sim, &t);
-            steps_get_windows(j.sim, &j.windows, nullptr);
-            j.t = t;
-            if (t >= j.t_end - 1e-12 * std::max(j.t_end, 1e-30)) {
-                rc = retire(srv, id);
-                if (rc) return rc;
-                ++nfin;
-                srv->batch_valid = false;
-            } else {
-                keep.push_back(id);
-            }
+        int rc = steps::batch_enqueue(g.batch, target.data());
+        if (rc) {
+            rc_first = rc;
+            break;
         }
-        if (!srv->batch_valid) srv->drop_batch();
-        srv->running.swap(keep);
+        g.enqueued = true;
+        any = true;
     }
-    if (running) *running = (int32_t)srv->running.size();
+    // wait for every enqueued batch, even after an error
+    for (Group &g : srv->groups) {
+        if (!g.enqueued) continue;
+        int rc = steps::batch_finish(g.batch);
+        if (rc && rc_first == STEPS_OK) rc_first = rc;
+        g.enqueued = false;
+    }
+    if (rc_first) return rc_first;
+    if (any) ++srv->rounds;
+    for (Group &g : srv->groups) {
+        int rc = sweep(g);
+        if (rc) return rc;
+    }
+    if (running) *running = srv->n_running;
     if (finished) *finished = nfin;
     return STEPS_OK;
 }
@@ -315,12 +387,14 @@ int steps_server_stats(const steps_server *srv, uint64_t *rounds, uint64_t *rebu
     if (rebuilds) *rebuilds = srv->rebuilds;
     if (launches) {
         uint64_t l = srv->launches;
-        uint64_t bl = 0;
-        if (srv->batch && steps_batch_info(srv->batch, nullptr, &bl, nullptr) == STEPS_OK) l += bl;
+        for (const Group &g : srv->groups) {
+            uint64_t bl = 0;
+            if (g.batch && steps_batch_info(g.batch, nullptr, &bl, nullptr) == STEPS_OK) l += bl;
+        }
         *launches = l;
     }
     if (queued) *queued = (int32_t)srv->queue.size();
-    if (running) *running = (int32_t)srv->running.size();
+    if (running) *running = srv->n_running;
     if (device_bytes) *device_bytes = srv->bytes_running;
     return STEPS_OK;
 }

@@ -38,10 +38,13 @@ class JobResult:
 
 class Prototypes:
     """One simulation per (generator, size bucket): meshes and tables are built
-    once and cloned per job."""
+    once and cloned per job. specialize = 1 compiles the step kernels for each
+    model structure here, when the first prototype of that structure is
+    created (clones and batches of the same structure reuse them)."""
 
-    def __init__(self, stream=None):
+    def __init__(self, stream=None, specialize: int = 1):
         self.stream = stream
+        self.specialize = specialize
         self._w = {}
         self._sim = {}
 
@@ -55,7 +58,7 @@ class Prototypes:
         key = (kind, size)
         if key not in self._sim:
             w = self.workload(kind, size)
-            s = capi.Simulation(w.verts, w.tets, w.model, 1, cuda_stream=self.stream)
+            s = capi.Simulation(w.verts, w.tets, w.model, 1, cuda_stream=self.stream, specialize=self.specialize)
             for r, m in w.reac_masks.items():
                 s.set_reac_mask(r, m)
             self._sim[key] = s
@@ -85,17 +88,19 @@ class Server:
     latency. The budget covers the prototypes and the running jobs."""
 
     def __init__(self, hbm_budget: int, max_jobs: int = 64, wave_windows: int = 16, block: int = 256,
-                 cuda_stream=None, specialize: int = -1):
+                 cuda_stream=None, specialize: int = 1):
         self.budget = int(hbm_budget)
         self.max_jobs = max_jobs
         self.wave_windows = wave_windows
         self.block = block
         self.stream = cuda_stream
-        # batches re-form as jobs come and go: by default a fixed block size (no autotuning
-        # windows on every re-formed batch) and the generic batched kernel (no run-time
-        # compilation between requests)
+        # batches re-form as jobs come and go: a fixed block size (no autotuning windows on
+        # every re-formed batch); by default jobs are grouped by model structure and each
+        # group runs the kernel compiled for its model when its prototype was created
+        # (specialize = 1), so nothing is compiled between requests; -1 runs one batch of
+        # every job on the generic kernel
         self.specialize = specialize
-        self.protos = Prototypes(cuda_stream)
+        self.protos = Prototypes(cuda_stream, specialize=1 if specialize >= 0 else 0)
         self.stats = {"waves": 0, "max_active": 0, "batch_rebuilds": 0, "launches": 0, "admit_waits": 0}
 
     def run(self, jobs, realtime: bool = True):

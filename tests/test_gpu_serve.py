@@ -25,16 +25,20 @@ def _jobs(n=16):
     return I.served_jobs(n, rate=400.0, seed=5, t_range=(0.5e-3, 6e-3), size_range=(2_000, 40_000))
 
 
-@pytest.mark.parametrize("realtime", [False, True])
-def test_each_job_same_alone_and_in_the_mix(serve, realtime):
+@pytest.mark.parametrize("realtime,specialize", [(False, 1), (True, 1), (False, -1)])
+def test_each_job_same_alone_and_in_the_mix(serve, realtime, specialize):
+    """specialize = 1: jobs grouped by model structure, each group on the
+    kernel compiled for its model, groups on streams of their own; -1: one
+    batch of every job on the generic kernel."""
     jobs = _jobs()
-    protos = serve.Prototypes()
+    protos = serve.Prototypes(specialize=1 if specialize >= 0 else 0)
     alone, _ = serve.run_alone(jobs, protos, realtime=False)
     # budget: the prototypes plus about three average jobs, so admission has to wait
     for j in jobs:
         protos.sim(j.kind, j.size)
     per_job = np.mean([protos.sim(j.kind, j.size).device_bytes for j in jobs])
-    srv = serve.Server(hbm_budget=int(protos.device_bytes() + 3 * per_job), max_jobs=6, wave_windows=8)
+    srv = serve.Server(hbm_budget=int(protos.device_bytes() + 3 * per_job), max_jobs=6, wave_windows=8,
+                       specialize=specialize)
     srv.protos = protos
     mixed = srv.run(jobs, realtime=realtime)
     for j in jobs:
@@ -59,8 +63,8 @@ def test_native_server_jobs_equal_alone_and_budget_admission(serve):
     ws = [I.config1(seed=3), I.config2(seed=9, nx=3, t_end=2e-3), I.config3(h=0.5e-6, t_end=0.1e-3)]
     protos = [capi.from_workload(w) for w in ws]
     specs = [(0, 11, 3.3e-3), (1, 12, 2.0e-3), (2, 13, 0.1e-3), (1, 14, 0.0), (0, 15, 1.48e-3), (2, 16, 0.071e-3)]
-    for budget, limit in [(0, 6), (1, 1)]:
-        srv = capi.NativeServer(device_budget=budget, max_jobs=4, wave_windows=5)
+    for budget, limit, spec in [(0, 6, -1), (1, 1, -1), (0, 6, 0), (0, 6, 1)]:
+        srv = capi.NativeServer(device_budget=budget, max_jobs=4, wave_windows=5, specialize=spec)
         ids = [srv.submit(protos[k], seed, ws[k].counts, t) for k, seed, t in specs]
         assert ids == list(range(len(specs)))
         assert all(srv.state(i)[0] == 0 for i in ids)
@@ -79,7 +83,7 @@ def test_native_server_jobs_equal_alone_and_budget_admission(serve):
             ref.set_counts(ws[k].counts)
             ref.run(t)
             assert windows == ref.windows
-            assert np.array_equal(got, ref.get_counts()), (budget, i)
+            assert np.array_equal(got, ref.get_counts()), (budget, spec, i)
             assert srv.state(i)[0] == 3
             with pytest.raises(capi.StepsError):
                 capi._check(capi.lib.steps_server_take_result(srv._h, i, None))
