@@ -13,10 +13,18 @@ from CUDA graphs). Metric: tet-updates/s = tets x windows / time.
   e2e       the same metric through the public C ABI with host buffers:
             steps_set_counts_all (H2D), steps_run, steps_get_counts_all (D2H),
             wall clock per step.
-  roofline  the step kernel: algorithmic bytes per launch / average launch time.
-  cpu_baseline  the CPU oracle (serial C, 1 core) on a bounded sample.
+  roofline  the step kernel. The box's working set sits in L2 and the kernel
+            is bound by instruction issue: bound "alu", warp instructions
+            (ncu count per launch) per second against 152 SMs x 4 schedulers
+            x 1 warp instruction per cycle x the sampled SM clock. Beside it,
+            `hbm`: algorithmic bytes per launch / average launch time against
+            the measured copy bandwidth, on 8S + 52 bytes per tet-update (FP64
+            split tables) and on the 8S + 36 bytes this design moves.
+  cpu_baseline  the CPU oracle on the host's cores (threaded windows, bit for
+            bit the serial oracle) on a bounded sample, with the single-core
+            figure, the core count and the CPU model.
 
---impl reference runs the CPU oracle as the reference arm.
+--impl reference runs the CPU oracle on all host cores as the reference arm.
 With torchrun (N > 1) every rank runs an independent replica on its own GPU
 (different seed): weak scaling, value = sum over ranks / max time.
 """
@@ -169,15 +177,81 @@ def reduce_over_ranks(ms: float, units: float):
     return float(t.item()), float(u.item())
 
 
-def oracle_rate(w, windows: int):
-    """Serial oracle on `windows` full windows of the workload (1 core)."""
+def oracle_rate(w, windows: int, threads: int = 1):
+    """Oracle (FP64) on `windows` full windows of the workload, on `threads`
+    host threads (threaded windows give the serial result bit for bit)."""
     import oracle
     o = oracle.from_workload(w, prec=64)
     t0 = time.perf_counter()
     for _ in range(windows):
-        o.step(o.tau)
+        o.step(o.tau, threads=threads)
     dt = time.perf_counter() - t0
     return w.n_tets * windows / dt, dt
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_baseline(w, windows_all: int, windows_one: int):
+    """The oracle on every host core and on one, bounded samples of the workload."""
+    cores = host_cores()
+    rate_all, dt_all = oracle_rate(w, windows_all, threads=cores)
+    rate_one, dt_one = oracle_rate(w, windows_one, threads=1)
+    return {"value": rate_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{windows_all} full windows of {w.name} ({dt_all:.1f} s) on {cores} threads, FP64",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "single_core": {"value": rate_one, "unit": UNIT, "cores": 1,
+                            "sample": f"{windows_one} full windows ({dt_one:.1f} s), serial C, FP64"}}
+
+
+def roofline(S: int, masked: bool, tets: int, kernel_s: float, peak: float, peak_kind: str, tr, sm_mhz,
+             issue_bound: bool):
+    """Roofline object of a plain step launch. hbm: algorithmic bytes per
+    tet-update, 8S + 52 (counts in and out, neighbours, FP64 split tables,
+    FP64 tau G, the volume factor) and the 8S + 36 (+4 with reaction masks)
+    this design moves (fixed-point thresholds), over the average launch time,
+    against the measured copy bandwidth. issue: warp instructions per launch
+    (ncu) over the launch time against the issue peak. The binding one leads."""
+    b52 = 8 * S + 52
+    b36 = 8 * S + 36 + (4 if masked else 0)
+    hbm = {"bound": "hbm", "achieved": tets * b52 / kernel_s / 1e9, "peak": peak, "unit": "GB/s",
+           "frac": tets * b52 / kernel_s / 1e9 / peak, "bytes_per_tet_update": b52,
+           "achieved_fixed_point": tets * b36 / kernel_s / 1e9, "frac_fixed_point": tets * b36 / kernel_s / 1e9 / peak,
+           "bytes_per_tet_update_fixed_point": b36, "peak_source": peak_kind,
+           "traffic": tr["bytes_per_launch"] if tr else None, "kernel_us_avg": kernel_s * 1e6}
+    iss = issue_roofline(tr, kernel_s, sm_mhz)
+    if issue_bound and iss is not None:
+        out = {"bound": "alu", "achieved": iss["achieved"], "peak": iss["peak"], "unit": "warp-inst/s",
+               "frac": iss["frac"], "traffic": hbm["traffic"],
+               "peak_source": f"SMs x 4 schedulers x 1 warp instruction/cycle x {iss['sm_mhz']:.0f} MHz (sampled)",
+               "warp_instructions_per_launch": iss["warp_instructions_per_launch"], "kernel_us_avg": kernel_s * 1e6,
+               "note": "working set in L2; bound by instruction issue (ncu issue slots and stalls in profiles/)",
+               "hbm": hbm}
+        return out
+    hbm["issue"] = iss
+    return hbm
 
 
 def measure_batched(args, capi, I, torch, peak):
@@ -223,17 +297,21 @@ def measure_batched(args, capi, I, torch, peak):
     w1 = np.array([s.windows for s in sims])
     units = float(((w1 - w0) * T).sum())
     launches = int(max(w1 - w0))
-    achieved = units * (8 * S + 36) / (ms / 1e3) / 1e9
+    achieved = units * (8 * S + 52) / (ms / 1e3) / 1e9
+    achieved36 = units * (8 * S + 36) / (ms / 1e3) / 1e9
     blk, _, tune = batch.info
     tr = profile_traffic("step_kernel_batch_config4_32rep")
-    # captured on 32 replicates (2,512,566 tets); traffic grows with the tets of a launch
-    traffic = tr["bytes_per_launch"] / 2512566 * float(T.sum()) if tr else None
+    # captured on 32 replicates (units_per_launch tets); traffic grows with the tets of a launch
+    traffic = tr["bytes_per_launch"] / tr["units_per_launch"] * float(T.sum()) if tr else None
     out = {"value": units / (ms / 1e3), "unit": UNIT, "replicates": len(sims), "tets": int(T.sum()),
            "kernel": "specialised" if batch.specialized else "generic",
            "tets_min": int(T.min()), "tets_max": int(T.max()), "ms_per_step": ms / steps, "steps": steps,
            "windows_per_step_max": launches / steps, "block": blk, "autotune_ms_per_window": tune,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": traffic, "traffic_note": "ncu DRAM bytes per launch on 32 replicates, scaled by tets"},
+                        "bytes_per_tet_update": 8 * S + 52, "achieved_fixed_point": achieved36,
+                        "frac_fixed_point": achieved36 / peak, "bytes_per_tet_update_fixed_point": 8 * S + 36,
+                        "traffic": traffic, "traffic_note": "ncu DRAM bytes per launch on 32 replicates, scaled by tets",
+                        "traffic_per_tet_update": (tr["bytes_per_launch"] / tr["units_per_launch"]) if tr else None},
            "setup_s": setup_s, "l2": "working set > L2; also flushed before each step",
            "step": "one batched run of 20 ms per member from its initial counts (reset outside the events)"}
     batch.close()
@@ -278,17 +356,13 @@ def measure_dendrite(args, capi, I, torch, peak):
     w1, _ = capi.steps_get_windows(sim._sim)
     windows = w1 - w0
     S = w.model.n_species
-    bytes_per_tet = 8 * S + 36 + (4 if w.reac_masks else 0)
     kernel_s = (ms / 1e3) / windows
-    achieved = w.n_tets * bytes_per_tet / kernel_s / 1e9
     tr = profile_traffic("step_kernel_dendrite")
     out = {"value": w.n_tets * windows / (ms / 1e3), "unit": UNIT, "workload": w.name, "tets": w.n_tets,
            "form": "plain", "kernel": "specialised" if sim.specialized else "generic",
            "species": S, "reactions": w.model.n_reac, "tau_us": sim.tau * 1e6, "sim_ms_per_step": args.dendrite_ms,
            "windows_per_step": windows / steps, "ms_per_step": ms / steps, "steps": steps,
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": tr["bytes_per_launch"] if tr else None, "bytes_per_tet_update": bytes_per_tet,
-                        "kernel_us_avg": kernel_s * 1e6, "issue": issue_roofline(tr, kernel_s, None)},
+           "roofline": roofline(S, bool(w.reac_masks), w.n_tets, kernel_s, peak, "measured", tr, None, False),
            "setup_s": setup_s, "l2": "working set > L2; also flushed before each step",
            "step": "steps_run over sim_ms_per_step from the initial counts (reset outside the events)"}
     sim.close()
@@ -382,9 +456,12 @@ def measure_dendrite_recording(args, capi, I, torch):
 
 
 def measure_served(args, capi, I):
-    """Served form: Poisson stream (50 jobs/s) of jobs from the config 1-3
-    generators, 2k-1M tets, t_end 1-100 ms, admitted by a device-memory budget,
-    continuously batched; the same jobs alone in plain form, one after another."""
+    """Served form: a Poisson stream (50 jobs/s) of jobs from the config 1-3
+    generators, 2k-1M tets, t_end 1-100 ms, admitted by a device-memory
+    budget, continuously batched (jobs grouped by model structure, each group
+    on the kernel compiled for its model when its prototype was created); the
+    same jobs alone in plain form, one after another. Then the same jobs at
+    saturation: all queued at once, served both ways."""
     import torch
     from paper_1610_02258_gb300 import serve
     jobs = I.served_jobs(args.served_jobs, rate=50.0, seed=21)
@@ -395,19 +472,72 @@ def measure_served(args, capi, I):
     setup_s = time.perf_counter() - t0
     free, total = torch.cuda.mem_get_info()
     budget = int(min(free * 0.8, 64 << 30))
-    srv = serve.Server(hbm_budget=budget, max_jobs=128, wave_windows=32)
-    srv.protos = protos
-    mixed = srv.run(jobs, realtime=True)
-    s_mixed = serve.summarize(mixed, srv.stats["makespan"])
-    alone, mk = serve.run_alone(jobs, protos, realtime=True)
-    s_alone = serve.summarize(alone, mk)
-    same = all(np.array_equal(mixed[j.job_id].counts, alone[j.job_id].counts) for j in jobs)
+    keys = ("throughput", "p50_s", "p99_s", "mean_s", "makespan_s")
+    out = {"jobs": len(jobs), "rate_jobs_per_s": 50.0, "hbm_budget_bytes": budget, "unit": UNIT,
+           "prototype_setup_s": setup_s, "kernel": "specialised per model structure (compiled with the prototypes)"}
+    same = True
+    for label, realtime in (("", True), ("saturated_", False)):
+        srv = serve.Server(hbm_budget=budget, max_jobs=128, wave_windows=32)
+        srv.protos = protos
+        mixed = srv.run(jobs, realtime=realtime)
+        s_mixed = serve.summarize(mixed, srv.stats["makespan"])
+        alone, mk = serve.run_alone(jobs, protos, realtime=realtime)
+        s_alone = serve.summarize(alone, mk)
+        same = same and all(np.array_equal(mixed[j.job_id].counts, alone[j.job_id].counts) for j in jobs)
+        out[label + "continuous"] = {k: s_mixed[k] for k in keys}
+        out[label + "continuous"].update({"max_active": srv.stats["max_active"], "waves": srv.stats["waves"],
+                                          "batch_rebuilds": srv.stats["batch_rebuilds"]})
+        out[label + "alone_plain"] = {k: s_alone[k] for k in keys}
+    out["saturated_note"] = "every job queued at time 0 (arrivals faster than capacity)"
+    out["results_identical"] = bool(same)
     protos.close()
-    return {"jobs": len(jobs), "rate_jobs_per_s": 50.0, "hbm_budget_bytes": budget,
-            "continuous": {k: s_mixed[k] for k in ("throughput", "p50_s", "p99_s", "mean_s", "makespan_s")},
-            "alone_plain": {k: s_alone[k] for k in ("throughput", "p50_s", "p99_s", "mean_s", "makespan_s")},
-            "unit": UNIT, "results_identical": bool(same), "max_active": srv.stats["max_active"],
-            "waves": srv.stats["waves"], "prototype_setup_s": setup_s}
+    return out
+
+
+def measure_sweeps(args, capi, I, torch):
+    """The paper's density and mesh-coarseness experiments (§3.1) on the box:
+    the benchmark network at 0.1x, 1x and 10x its densities, and the box
+    meshed with 8, 17 and 26 cubes across (h = 10/8, 10/17, 10/26 um; about
+    31k, 295k and 1.05M tets) at the benchmark densities. Each point: one
+    20 ms run from the initial counts, device time per window."""
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = {"density": [], "mesh": []}
+
+    def timed(w):
+        counts = np.ascontiguousarray(w.counts, np.int32)
+        sim = capi.from_workload(w, cuda_stream=stream.cuda_stream)
+        sim.set_counts(counts)
+        sim.run(sim.time + 2e-3)  # warm
+        ms, wins = 0.0, 0
+        for _ in range(2):
+            sim.set_counts(counts)
+            flush.zero_()
+            w0 = sim.windows
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.run(sim.time + 20e-3)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            wins += sim.windows - w0
+        out = {"tets": w.n_tets, "molecules_per_tet": float(counts.sum()) / w.n_tets, "tau_us": sim.tau * 1e6,
+               "us_per_window": 1e3 * ms / wins, "value": w.n_tets * wins / (ms / 1e3), "unit": UNIT,
+               "kernel": "specialised" if sim.specialized else "generic"}
+        sim.close()
+        return out
+
+    base = I.config2()
+    for scale in (0.1, 1.0, 10.0):
+        r = timed(base if scale == 1.0 else I.config2(density_scale=scale))
+        r["density_scale"] = scale
+        res["density"].append(r)
+    for n in (8, 17, 26):
+        w = base if n == 17 else I.config2(nx=10 * n, ny=n, nz=n, h=10.0 / n * I.UM)
+        r = timed(w)
+        r["cubes_across"] = n
+        res["mesh"].append(r)
+    return res
 
 
 def run_reference(args):
@@ -419,11 +549,12 @@ def run_reference(args):
     from paper_1610_02258_gb300 import inputs as I
     w = I.config2()
     windows = 5
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle_rate(w, 1)
+        oracle_rate(w, 1, threads=cores)
     times = []
     for _ in range(args.steps):
-        _, dt = oracle_rate(w, windows)
+        _, dt = oracle_rate(w, windows, threads=cores)
         times.append(dt)
     value = w.n_tets * windows * args.steps / sum(times)
     line = {
@@ -432,8 +563,10 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "tets": w.n_tets, "species": w.model.n_species,
                    "reactions": w.model.n_reac, "sample": f"{windows} full windows per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{windows} full windows of {w.name} per step, serial C oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{windows} full windows of {w.name} per step, C oracle on {cores} threads "
+                                   "(threaded windows, the serial result bit for bit)",
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -521,12 +654,9 @@ def run_ours(args):
             torch.distributed.barrier()
         return
     S = w.model.n_species
-    bytes_per_tet = 8 * S + 36 + (4 if w.reac_masks else 0)
     kernel_s = (ms / 1e3) / windows
-    achieved = w.n_tets * bytes_per_tet / kernel_s / 1e9
     peak, peak_kind = _peaks()
     tr = profile_traffic("step_kernel_dendrite" if args.workload == "dendrite" else "step_kernel_config2")
-    traffic = tr["bytes_per_launch"] if tr else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
@@ -540,10 +670,8 @@ def run_ours(args):
                    "parallelism": f"replicas{world}"},
         "e2e": e2e,
         "gpu_launches": int(l1 - l0),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_source": peak_kind,
-                     "bytes_per_tet_update": bytes_per_tet, "kernel_us_avg": kernel_s * 1e6,
-                     "issue": issue_roofline(tr, kernel_s, clk["sm_mhz"] if clk else None)},
+        "roofline": roofline(S, bool(w.reac_masks), w.n_tets, kernel_s, peak, peak_kind, tr,
+                             clk["sm_mhz"] if clk else None, issue_bound=args.workload != "dendrite"),
         "clocks": clk,
     }
     if world == 1 and not args.no_forms and args.workload == "irregular-box":
@@ -554,11 +682,10 @@ def run_ours(args):
                                                        if args.dendrite_ms > 0 else None),
                          "batched": measure_batched(args, capi, I, torch, peak) if args.batch_replicates > 0 else None,
                          "served": measure_served(args, capi, I) if args.served_jobs > 0 else None}
+    if world == 1 and args.sweep:
+        line["sweeps"] = measure_sweeps(args, capi, I, torch)
     if world == 1 and not args.no_cpu_baseline:
-        cpu_windows = args.cpu_windows
-        rate, dt = oracle_rate(w, cpu_windows)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{cpu_windows} full windows of {w.name} ({dt:.1f} s), serial C, FP64"}
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_windows, max(5, args.cpu_windows // 4))
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
@@ -574,7 +701,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--batch-replicates", type=int, default=256)
-    ap.add_argument("--served-jobs", type=int, default=200)
+    ap.add_argument("--served-jobs", type=int, default=1000)
+    ap.add_argument("--sweep", action="store_true",
+                    help="add the density (0.1x/1x/10x) and mesh-size (8/17/26 cubes across) sweeps of the box")
     ap.add_argument("--workload", default="irregular-box", choices=["irregular-box", "dendrite"],
                     help="plain workload of the headline line: the 294,780-tet jittered box (default) or the "
                          "1.03M-tet dendrite")

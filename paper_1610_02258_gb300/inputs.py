@@ -351,18 +351,20 @@ def config1(seed: int = 3):
 
 
 def config2(seed: int = 3, nx: int = 170, ny: int = 17, nz: int = 17, t_end: float = 20e-3,
-            net_seed: int = 5):
+            net_seed: int = 5, h: float = None, density_scale: float = 1.0):
     """100x10x10 um box of 170x17x17 cubes (h = 10/17 um) x 6 tets = 294,780
     tets, vertices jittered by 20% of the spacing; random 10-species,
-    20-reaction network; densities U[1, 100] /um^3 per species; 20 ms."""
-    h = 10.0 / 17.0 * UM
+    20-reaction network; densities U[1, 100] /um^3 per species (times
+    density_scale); 20 ms. h sets another cube edge (the mesh-coarseness
+    experiment: the same box with nx = 10 n, ny = nz = n, h = 10/n um)."""
+    h = 10.0 / 17.0 * UM if h is None else h
     verts, tets = kuhn_box_mesh(nx, ny, nz, h)
     verts = jitter_box_vertices(verts, h, 0.2, seed=1)
     m = random_network(net_seed)
     nt = tets.shape[0]
     rng = np.random.default_rng(2)
     vol_um3 = nx * ny * nz * (h / UM) ** 3
-    dens = rng.uniform(1.0, 100.0, size=m.n_species)
+    dens = rng.uniform(1.0, 100.0, size=m.n_species) * density_scale
     counts = np.zeros((m.n_species, nt), np.int32)
     for s in range(m.n_species):
         counts[s] = place_uniform(int(round(dens[s] * vol_um3)), nt, seed=100 + s)
