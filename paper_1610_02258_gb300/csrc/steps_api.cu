@@ -883,7 +883,9 @@ struct steps_batch {
     bool use_graph = true;
     int max_S = 1, max_R = 0;
     bool any_order0 = false;
-    RepEntry *h_reps = nullptr;  // pinned host mirror
+    RepEntry *h_reps = nullptr;  // pinned host mirror (full windows)
+    RepEntry *h_last = nullptr;  // pinned host table of the shortened last windows: a second buffer, so
+                                 // that filling it cannot change h_reps while its upload is still queued
     RepEntry *d_reps = nullptr;
     uint32_t *d_err = nullptr;
     uint32_t *h_err = nullptr;   // pinned copy of the error word, read after the stream completes
@@ -910,6 +912,7 @@ struct steps_batch {
         cudaFree(d_reps);
         cudaFree(d_err);
         cudaFreeHost(h_err);
+        cudaFreeHost(h_last);
         cudaFreeHost(h_reps);
     }
 
@@ -1044,6 +1047,7 @@ int steps_batch_create(steps_sim *const *members, int32_t n, const steps_batch_o
         b->any_order0 = b->any_order0 || members[j]->model.dev.order0 != 0u;
     }
     if (!cuda_ok(cudaMallocHost((void **)&b->h_reps, sizeof(RepEntry) * n), "steps_batch_create: host alloc") ||
+        !cuda_ok(cudaMallocHost((void **)&b->h_last, sizeof(RepEntry) * n), "steps_batch_create: host alloc") ||
         !cuda_ok(cudaMallocHost((void **)&b->h_err, 4), "steps_batch_create: host alloc") ||
         !cuda_ok(cudaMalloc((void **)&b->d_reps, sizeof(RepEntry) * n), "steps_batch_create: alloc") ||
         !cuda_ok(cudaMalloc((void **)&b->d_err, 4), "steps_batch_create: alloc") ||
@@ -1186,11 +1190,13 @@ int batch_enqueue(steps_batch *b, const double *t_end) {
     }
     rc = b->run_windows(b->block, nmax - done);
     if (rc) return rc;
-    // shortened last windows
+    // shortened last windows: their table goes into the second pinned buffer
+    // (h_reps may still be read by its queued upload)
     bool any_partial = false;
     for (size_t j = 0; j < n; ++j) {
         steps_sim *m = b->members[j];
-        RepEntry &e = b->h_reps[j];
+        RepEntry &e = b->h_last[j];
+        e = b->h_reps[j];
         const uint64_t w = m->k_total + (uint64_t)nfull[j];
         e.args.window = w;
         e.parity = (uint32_t)(m->cur ^ (int)(nfull[j] & 1));
@@ -1206,7 +1212,7 @@ int batch_enqueue(steps_batch *b, const double *t_end) {
         }
     }
     if (any_partial) {
-        if (!cuda_ok(cudaMemcpyAsync(b->d_reps, b->h_reps, sizeof(RepEntry) * n, cudaMemcpyHostToDevice, b->stream),
+        if (!cuda_ok(cudaMemcpyAsync(b->d_reps, b->h_last, sizeof(RepEntry) * n, cudaMemcpyHostToDevice, b->stream),
                      "steps_batch_run: upload"))
             return STEPS_ERR_CUDA;
         rc = b->run_windows(b->block, 1);

@@ -167,3 +167,29 @@ def test_full_size_batched_configuration_sampled_against_oracle(capi):
         assert sims[j].windows == o.windows
         assert np.array_equal(sims[j].get_counts(), o.get_counts()), j
     b.close()
+
+
+def test_batch_tables_survive_a_busy_stream(capi):
+    """Rounds in which every member ends off its window grid (a shortened
+    window after its full ones), each run queued behind ~0.3 ms of other
+    work on the batch's stream, so the uploads of the window tables run long
+    after the host has filled them in: the full-window table must not change
+    under its queued upload. Every member equals its runs alone."""
+    import torch
+    ws = [I.config1(seed=20 + j) for j in range(6)] + [I.config2(seed=30 + j, nx=2, t_end=1e-3) for j in range(3)]
+    members = [capi.from_workload(w) for w in ws]
+    alone = [capi.from_workload(w) for w in ws]
+    busy = torch.cuda.Stream()
+    b = capi.Batch(members, block=256, use_graph=False, cuda_stream=busy.cuda_stream)
+    big = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    for r in range(4):
+        targets = [m.time + (1 + (j + r) % 3 + 0.5) * m.tau for j, m in enumerate(members)]
+        with torch.cuda.stream(busy):
+            big.zero_()
+            big.add_(1)
+        b.run(targets)
+        for s, t in zip(alone, targets):
+            s.run(t)
+        for j, (m, s) in enumerate(zip(members, alone)):
+            assert m.windows == s.windows and m.time == s.time, (r, j)
+            assert np.array_equal(m.get_counts(), s.get_counts()), (r, j)
