@@ -69,6 +69,7 @@ def lib():
         L.orc_logf32.restype = ctypes.c_float
         L.orc_sample_faces.argtypes = [c_u64, c_u64, c_u32, c_u32, c_i32, P, P]
         L.orc_sample_faces.restype = c_u32
+        L.orc_sample_bulk.argtypes = [c_u64, c_u64, c_u32, ctypes.c_int, c_i32, P, P]
         L.orc_logf32_array.argtypes = [P, c_i64, P]
         L.orc_philox_array.argtypes = [c_u64, P, c_i64, P]
         _lib = L
@@ -129,6 +130,18 @@ def sample_faces(seed, window, tet, w0, M, T):
     out = np.zeros(4, np.int32)
     used = lib().orc_sample_faces(seed, window, tet, w0, M, _p(Ta), _p(out))
     return out, int(used)
+
+
+BULK_MIN = 8  # trial molecules of a species in a tet from which the oracle draws by bit planes
+
+
+def sample_bulk(seed, window, tet, species, M, T):
+    """Faces chosen by M trial molecules of one species drawing by bit planes
+    (the path of M >= BULK_MIN); returns counts per face [4]."""
+    Ta = np.ascontiguousarray(T, np.uint32)
+    out = np.zeros(4, np.int32)
+    lib().orc_sample_bulk(seed, window, tet, int(species), int(M), _p(Ta), _p(out))
+    return out
 
 
 class OracleSim:

@@ -39,7 +39,13 @@
  *     x falls in [T_{f-1}, T_f), T being cumulative fixed-point thresholds
  *     (2^31 * p * cumulative face-rate share); it stays when x >= T_3. This is
  *     exactly Bin(M, p) leaving followed by Multinomial(n, g_f/G), with p and
- *     the shares quantised to 2^-31.
+ *     the shares quantised to 2^-31. Where x comes from: a species with fewer
+ *     than ORC_BULK_MIN trial molecules in a tet takes one word per molecule
+ *     from the tet's word stream (species in order); one with more takes its
+ *     molecules in groups of 32, whose x are assembled from 31 bit planes
+ *     (plane k is bit 30 - k of every x; bit j of the plane's word belongs to
+ *     molecule j of the group). Either way x is uniform on [0, 2^31), so the
+ *     law is the same.
  *   - reaction propensities: order 0 a = k N_A V, order 1 a = k N_X, order 2
  *     a = k/(N_A V) N_X N_Y, homodimer a = k/(N_A V) N_X (N_X - 1).
  */
@@ -54,7 +60,8 @@
 #define ORC_MAXR 32
 #define ORC_AVOGADRO 6.02214076e23
 
-enum { ORC_PURPOSE_REAC = 1, ORC_PURPOSE_ROUND = 2, ORC_PURPOSE_DIFF = 3 };
+enum { ORC_PURPOSE_REAC = 1, ORC_PURPOSE_ROUND = 2, ORC_PURPOSE_DIFF = 3, ORC_PURPOSE_BULK = 4 };
+#define ORC_BULK_MIN 8 /* trial molecules of a species in a tet from which it draws by bit planes */
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_MESH = -2, ORC_ERR_MODEL = -3, ORC_ERR_OOM = -4 };
 
 /* ------------------------------------------------------------------------ */
@@ -90,6 +97,20 @@ static void draw4(uint64_t seed, uint64_t window, uint32_t tet, uint32_t idx, ui
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t ctr[4] = {(uint32_t)window, tet, idx,
                        (purpose << 28) | ((uint32_t)(window >> 32) & 0x0FFFFFFFu)};
+    orc_philox4x32_10(key, ctr, out);
+}
+
+/* Bit planes of the trial molecules of species sp in group g (molecules
+ * 32g .. 32g + 31) of a tet: block blk holds planes 4 blk .. 4 blk + 3.
+ * Counter = (window low 32 bits, original tet id, g << 3 | blk,
+ * purpose << 28 | sp << 23 | window index bits 32..54). */
+static void draw4_bulk(uint64_t seed, uint64_t window, uint32_t tet, int sp, uint32_t g, uint32_t blk,
+                       uint32_t out[4])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)window, tet, (g << 3) | blk,
+                       ((uint32_t)ORC_PURPOSE_BULK << 28) | ((uint32_t)sp << 23) |
+                           ((uint32_t)(window >> 32) & 0x007FFFFFu)};
     orc_philox4x32_10(key, ctr, out);
 }
 
@@ -549,6 +570,39 @@ uint32_t orc_sample_faces(uint64_t seed, uint64_t window, uint32_t tet, uint32_t
     return (uint32_t)M;
 }
 
+/* The same decisions for a species with M >= ORC_BULK_MIN trial molecules:
+ * molecule j of group g takes x = sum over planes k = 0..30 of
+ * (bit j of plane k) << (30 - k), and goes through the first face f with
+ * x < T_f (stays if x >= T_3). Adds the molecules sent through each face to
+ * out[]. */
+void orc_sample_bulk(uint64_t seed, uint64_t window, uint32_t tet, int sp, int32_t M, const uint32_t T[4],
+                     int32_t out[4])
+{
+    if (M <= 0 || T[3] == 0) return;
+    for (int64_t g = 0; 32 * g < (int64_t)M; ++g) {
+        int m = (int64_t)M - 32 * g < 32 ? (int)((int64_t)M - 32 * g) : 32;
+        uint32_t plane[32];
+        for (uint32_t blk = 0; blk < 8; ++blk) draw4_bulk(seed, window, tet, sp, (uint32_t)g, blk, plane + 4 * blk);
+        for (int j = 0; j < m; ++j) {
+            uint32_t x = 0;
+            for (int k = 0; k < 31; ++k) x |= ((plane[k] >> j) & 1u) << (30 - k);
+            for (int f = 0; f < 4; ++f) {
+                if (x < T[f]) { out[f] += 1; break; }
+            }
+        }
+    }
+}
+
+/* The diffusion draws of species sp with M trial molecules in tet i: by bit
+ * planes from ORC_BULK_MIN molecules on, else from the tet's word stream at
+ * word *w (advanced past the words used). */
+static void sample_species(const orc_sim *s, int64_t i, int sp, int32_t M, const uint32_t T[4], uint32_t *w,
+                           int32_t leave[4])
+{
+    if (M >= ORC_BULK_MIN) orc_sample_bulk(s->seed, s->k_total, (uint32_t)i, sp, M, T, leave);
+    else *w += orc_sample_faces(s->seed, s->k_total, (uint32_t)i, *w, M, T, leave);
+}
+
 /* Fixed-point species scale for a window of length tau_k:
  * R_S = floor(2^31 * (D_S / Dmax) * (tau_k / tau)), clamped to [0, 2^31]. */
 static uint32_t species_scale(const orc_sim *s, int sp, double tau_k)
@@ -592,15 +646,15 @@ static void window(orc_sim *s, double tau_k)
         for (int sp = 0; sp < S; ++sp) N[sp] = s->cnt[(size_t)sp * nt + i];
         /* reaction SSA operator */
         reaction_phase(s, i, tau_k, inv_tau_k, N, M, &s->events);
-        /* diffusion operator: every diffusive species in species order draws
-         * from one per-tet word stream */
+        /* diffusion operator: species in order; a species with few trial
+         * molecules draws from the tet's word stream, one with many by bit planes */
         uint32_t w = 0;
         for (int sp = 0; sp < S; ++sp) {
             int32_t leave[4] = {0, 0, 0, 0};
             if (s->D[sp] > 0.0) {
                 uint32_t T[4];
                 species_thresholds(s, i, scale[sp], T);
-                w += orc_sample_faces(s->seed, s->k_total, (uint32_t)i, w, M[sp], T, leave);
+                sample_species(s, i, sp, M[sp], T, &w, leave);
             }
             int32_t n = leave[0] + leave[1] + leave[2] + leave[3];
             s->nxt[(size_t)sp * nt + i] += N[sp] - n;
@@ -668,7 +722,7 @@ static void par_tet_pass1(orc_par_job *job, int64_t i, int64_t *events)
         if (s->D[sp] > 0.0) {
             uint32_t T[4];
             species_thresholds(s, i, job->scale[sp], T);
-            w += orc_sample_faces(s->seed, s->k_total, (uint32_t)i, w, M[sp], T, leave);
+            sample_species(s, i, sp, M[sp], T, &w, leave);
         }
         int32_t n = leave[0] + leave[1] + leave[2] + leave[3];
         s->nxt[(size_t)sp * nt + i] = N[sp] - n;

@@ -49,8 +49,11 @@ def _sim(verts, tets, model, counts, seed, occ=OCC, prec=64, masks=None):
 
 @pytest.mark.parametrize("occ,prec", MODES)
 def test_conservation_every_window(occ, prec):
+    """A + B <-> C with kf = 1e8 /M/s (about 70 events per window on the
+    cuboid, so reactions surely fire): A + C and B + C are conserved."""
     w = I.config1()
-    sim = _sim(w.verts, w.tets, w.model, w.counts, 9, occ, prec)
+    fast = I.model_from_lists(["A", "B", "C"], [1e-11] * 3, [(["A", "B"], ["C"], 1e8), (["C"], ["A", "B"], 10.0)])
+    sim = _sim(w.verts, w.tets, fast, w.counts, 9, occ, prec)
     tot = w.counts.sum(axis=1)
     events = 0
     for _ in range(6):
