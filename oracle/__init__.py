@@ -132,7 +132,7 @@ def sample_faces(seed, window, tet, w0, M, T):
     return out, int(used)
 
 
-BULK_MIN = 8  # trial molecules of a species in a tet from which the oracle draws by bit planes
+BULK_MIN = 16  # trial molecules of a species in a tet from which the oracle draws by bit planes
 
 
 def sample_bulk(seed, window, tet, species, M, T):

@@ -61,7 +61,7 @@
 #define ORC_AVOGADRO 6.02214076e23
 
 enum { ORC_PURPOSE_REAC = 1, ORC_PURPOSE_ROUND = 2, ORC_PURPOSE_DIFF = 3, ORC_PURPOSE_BULK = 4 };
-#define ORC_BULK_MIN 8 /* trial molecules of a species in a tet from which it draws by bit planes */
+#define ORC_BULK_MIN 16 /* trial molecules of a species in a tet from which it draws by bit planes */
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_MESH = -2, ORC_ERR_MODEL = -3, ORC_ERR_OOM = -4 };
 
 /* ------------------------------------------------------------------------ */

@@ -35,6 +35,9 @@ constexpr int64_t kWindowBatch = 1 << 16;
 constexpr uint32_t kPurposeReac = 1;
 constexpr uint32_t kPurposeRound = 2;
 constexpr uint32_t kPurposeDiff = 3;
+constexpr uint32_t kPurposeBulk = 4;  // bit planes of species with many trial molecules in a tet
+// trial molecules of a species in a tet from which it draws by bit planes
+constexpr int32_t kBulkMin = 16;
 
 // Reaction kinds by propensity form.
 enum ReacType : int8_t { kOrder0 = 0, kOrder1 = 1, kOrder2 = 2, kDimer = 3 };

@@ -359,6 +359,71 @@ __device__ __forceinline__ void species_thresholds(const uint4 &A, uint32_t R, u
     T3 = (uint32_t)(((uint64_t)A.w * R) >> 31);
 }
 
+// One threshold comparison x < T over a group of 32 molecules, one bit plane
+// at a time (plane k carries bit 30 - k of every molecule's x, bit j of the
+// word for molecule j): where the plane's bit of x differs from T's, the
+// comparison is decided (x < T where x has 0 and T has 1); it stays open
+// while they agree. und: molecules still open; lt: decided x < T.
+__device__ __forceinline__ void plane_compare(uint32_t T, int sh, uint32_t R, uint32_t &und, uint32_t &lt) {
+    const uint32_t tb = 0u - ((T >> sh) & 1u);  // all ones where T's bit is 1
+    lt |= und & ~R & tb;
+    und &= ~(R ^ tb);
+}
+
+// Diffusion draws of a species with M >= kBulkMin trial molecules in one tet
+// (Algorithm 1, diffusion operator): each trial molecule compares a uniform
+// 31-bit x with the cumulative thresholds T_0..T_3 and goes through the
+// first face f with x < T_f (stays if x >= T_3), exactly as one word per
+// molecule would, but x is assembled from bit planes: groups of 32
+// molecules take the words of Philox blocks (window, tet, g << 3 | blk,
+// bulk purpose | species << 23 | window high bits), plane k = word k of the
+// group. Planes are drawn only until every comparison of the group is
+// decided (a comparison still open after all 31 planes has x = T: not less).
+// The movers go to the neighbours' entries of nxt, one atomic add per face;
+// returns how many left.
+__device__ __forceinline__ int32_t bulk_species(const StepArgs &a, int s, int32_t M, const uint4 A, uint32_t Rs,
+                                             const int4 nb, uint32_t key_tet, uint32_t c0, uint32_t c3) {
+    uint32_t T0, T1, T2, T3;
+    species_thresholds(A, Rs, T0, T1, T2, T3);
+    const uint32_t c3b = (kPurposeBulk << 28) | ((uint32_t)s << 23) | (c3 & 0x007FFFFFu);
+    int32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+    for (uint32_t g = 0; 32u * g < (uint32_t)M; ++g) {
+        const uint32_t m = min(32u, (uint32_t)M - 32u * g);
+        const uint32_t valid = m == 32u ? 0xFFFFFFFFu : (1u << m) - 1u;
+        // T_f = 2^31: every x < T_f; T_f = 0: none
+        uint32_t l0 = T0 >= 0x80000000u ? valid : 0u, u0 = (T0 >= 0x80000000u || T0 == 0u) ? 0u : valid;
+        uint32_t l1 = T1 >= 0x80000000u ? valid : 0u, u1 = (T1 >= 0x80000000u || T1 == 0u) ? 0u : valid;
+        uint32_t l2 = T2 >= 0x80000000u ? valid : 0u, u2 = (T2 >= 0x80000000u || T2 == 0u) ? 0u : valid;
+        uint32_t l3 = T3 >= 0x80000000u ? valid : 0u, u3 = (T3 >= 0x80000000u || T3 == 0u) ? 0u : valid;
+        for (uint32_t blk = 0; blk < 8u && (u0 | u1 | u2 | u3); ++blk) {
+            const uint4 r = philox4x32_10(a.key0, a.key1, c0, key_tet, (g << 3) | blk, c3b);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = 4 * (int)blk + q;
+                if (k <= 30) {
+                    const uint32_t R = word_of(r, (uint32_t)q);
+                    const int sh = 30 - k;
+                    plane_compare(T0, sh, R, u0, l0);
+                    plane_compare(T1, sh, R, u1, l1);
+                    plane_compare(T2, sh, R, u2, l2);
+                    plane_compare(T3, sh, R, u3, l3);
+                }
+            }
+        }
+        // cumulative thresholds: l0 within l1 within l2 within l3
+        n0 += __popc(l0);
+        n1 += __popc(l1 & ~l0);
+        n2 += __popc(l2 & ~l1);
+        n3 += __popc(l3 & ~l2);
+    }
+    int32_t *row = a.nxt + (size_t)s * (size_t)a.Tpad;
+    if (n0) atomicAdd(row + nb.x, n0);
+    if (n1) atomicAdd(row + nb.y, n1);
+    if (n2) atomicAdd(row + nb.z, n2);
+    if (n3) atomicAdd(row + nb.w, n3);
+    return n0 + n1 + n2 + n3;
+}
+
 // Per-warp work state of the diffusion operator. The warp's chunk holds up
 // to 32 tets; their trial molecules form one stream per tet (species in
 // order), cut into Philox blocks of 4 words. Block b of the chunk belongs to
@@ -718,8 +783,10 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
                                          q_pick[t], q_dt[t], O, tS, touched);
 
         // trial counts: species that may hold molecules (non-zero at the start, or
-        // changed by a reaction), diffusive, with a non-zero leave threshold
-        uint32_t W = 0, hm = 0;
+        // changed by a reaction), diffusive, with a non-zero leave threshold.
+        // Species with kBulkMin or more trial molecules draw by bit planes here
+        // (their movers leave at once); the others join the tet's word stream.
+        uint32_t W = 0, hm = 0, bm = 0;
         if (valid) {
             uint32_t walk = (s_nz[t] | touched) & P::diffusive(m);
             const uint32_t Aw = s_thr[t].w;
@@ -731,8 +798,12 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
                     const int32_t M = cnt_all[s * BLOCK + t];
                     if (M > 0 && (uint32_t)(((uint64_t)Aw * s_scale[s]) >> 31) != 0u) {
                         trial_all[s * tstride + t] = M;
-                        hm |= 1u << s;
-                        W += (uint32_t)M;
+                        if (M >= kBulkMin) {
+                            bm |= 1u << s;
+                        } else {
+                            hm |= 1u << s;
+                            W += (uint32_t)M;
+                        }
                     }
                 }
             } else {
@@ -746,11 +817,24 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
                                                   s_tet[t], c0, c3, rblk, rb);
                     if (M > 0) {
                         trial_all[s * tstride + t] = M;
-                        hm |= 1u << s;
-                        W += (uint32_t)M;
+                        if (M >= kBulkMin) {
+                            bm |= 1u << s;
+                        } else {
+                            hm |= 1u << s;
+                            W += (uint32_t)M;
+                        }
                     }
                 }
             }
+        }
+        // species with many trial molecules: bit-plane draws by the lane that
+        // owns the tet, movers sent now (they are rare unless counts are high,
+        // and then every lane has some)
+        while (bm) {
+            const int s = __ffs(bm) - 1;
+            bm &= bm - 1;
+            cnt_all[s * BLOCK + t] -= bulk_species(a, s, trial_all[s * tstride + t], s_thr[t], s_scale[s], s_nbr[t],
+                                                   s_tet[t], c0, c3);
         }
         // the chunk's Philox blocks: exclusive prefix of the lanes' block counts
         const uint32_t nb = (W + 3u) >> 2;

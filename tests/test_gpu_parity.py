@@ -290,6 +290,35 @@ def test_edge_large_counts_and_p_equal_one(capi):
     assert np.array_equal(gc, oc) and gc.sum() == 100000
 
 
+@pytest.mark.parametrize("spec", [-1, 1])
+def test_dense_box_bit_exact(capi, spec):
+    """The benchmark network at ten times its densities on a 6x17x17-cube
+    box (10,404 tets, ~146 molecules per tet): the denser species of most
+    tets hold 16 or more trial molecules and draw by bit planes, the rest by
+    one word per molecule, with reactions and occupancy rounding on; generic and
+    model-specialised kernels, a run ending off the window grid."""
+    w = I.config2(nx=6, density_scale=10.0, t_end=1.7e-3)
+    assert w.counts.sum() / w.n_tets > 100
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, w.model, w.counts, 19, [0.9e-3, w.t_end], specialize=spec)
+    assert g.specialized == (spec == 1)
+    assert o.events > 10000
+    assert np.array_equal(gc, oc)
+
+
+def test_bulk_threshold_boundary_bit_exact(capi):
+    """Counts of 15, 16, 17, 31, 32, 33 and 64 molecules of one species in
+    single tets (both sides of the bit-plane threshold and of a group of 32),
+    two species diffusing at different rates, a shortened window."""
+    w = I.config1()
+    m = I.model_from_lists(["A", "B"], [1e-11, 2.7e-12], [])
+    c = np.zeros((2, w.n_tets), np.int32)
+    for j, n in enumerate([15, 16, 17, 31, 32, 33, 64]):
+        c[0, 100 + 37 * j] = n
+        c[1, 90 + 41 * j] = n
+    gc, oc, *_ = run_both(capi, w.verts, w.tets, m, c, 4, [1.5e-3, 2.6e-3])
+    assert np.array_equal(gc, oc)
+
+
 def max_size_model(seed: int = 17):
     """32 species and 32 reactions, the most a model may have: order-0 influx
     (one masked to a region), a dimerisation 2X -> Y, reactions that change 6
