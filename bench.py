@@ -674,6 +674,8 @@ def run_ours(args):
                              clk["sm_mhz"] if clk else None, issue_bound=args.workload != "dendrite"),
         "clocks": clk,
     }
+    if world == 1 and args.sweep:
+        line["sweeps"] = measure_sweeps(args, capi, I, torch)
     if world == 1 and not args.no_forms and args.workload == "irregular-box":
         line["forms"] = {"plain": {"value": value, "unit": UNIT, "workload": w.name},
                          "plain_cuboid": measure_cuboid(args, capi, I, torch),
@@ -682,8 +684,6 @@ def run_ours(args):
                                                        if args.dendrite_ms > 0 else None),
                          "batched": measure_batched(args, capi, I, torch, peak) if args.batch_replicates > 0 else None,
                          "served": measure_served(args, capi, I) if args.served_jobs > 0 else None}
-    if world == 1 and args.sweep:
-        line["sweeps"] = measure_sweeps(args, capi, I, torch)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_windows, max(5, args.cpu_windows // 4))
     print(json.dumps(line), flush=True)
