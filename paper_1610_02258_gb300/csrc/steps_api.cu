@@ -1150,7 +1150,10 @@ int batch_enqueue(steps_batch *b, const double *t_end) {
     int64_t done = 0;
     int rc = STEPS_OK;
     if (b->autotune && nmax >= 12) {
-        // time 3 windows at each candidate block size, keep the fastest
+        // time the candidate block sizes on alternating windows (one warm window
+        // each, then two rounds of one timed window each), so that the state's
+        // slow drift over the run cancels; keep 256 unless another is more than
+        // 2 % faster
         const int cand[3] = {128, 256, 512};
         b->tune_ms.assign(3, 0.f);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1159,32 +1162,41 @@ int batch_enqueue(steps_batch *b, const double *t_end) {
             if (e0) cudaEventDestroy(e0);
             return STEPS_ERR_CUDA;
         }
-        float best = 1e30f;
-        int best_b = b->block;
-        for (int c = 0; c < 3 && rc == STEPS_OK; ++c) {
-            rc = b->build_work(cand[c]);
-            if (rc) break;
-            rc = b->run_windows(cand[c], 1);  // warm
-            if (rc) break;
-            float ms = 0.f;
-            if (!cuda_ok(cudaEventRecord(e0, b->stream), "steps_batch_run: autotuner") ||
-                (rc = b->run_windows(cand[c], 3)) != STEPS_OK ||
-                !cuda_ok(cudaEventRecord(e1, b->stream), "steps_batch_run: autotuner") ||
-                !cuda_ok(cudaEventSynchronize(e1), "steps_batch_run: autotuner") ||
-                !cuda_ok(cudaEventElapsedTime(&ms, e0, e1), "steps_batch_run: autotuner")) {
-                if (rc == STEPS_OK) rc = STEPS_ERR_CUDA;
-                break;
+        float total[3] = {0.f, 0.f, 0.f};
+        for (int round = 0; round < 2 && rc == STEPS_OK; ++round) {
+            for (int c = 0; c < 3 && rc == STEPS_OK; ++c) {
+                rc = b->build_work(cand[c]);
+                if (rc) break;
+                if (round == 0) {
+                    rc = b->run_windows(cand[c], 1);  // warm
+                    if (rc) break;
+                    done += 1;
+                }
+                float ms = 0.f;
+                if (!cuda_ok(cudaEventRecord(e0, b->stream), "steps_batch_run: autotuner") ||
+                    (rc = b->run_windows(cand[c], 1)) != STEPS_OK ||
+                    !cuda_ok(cudaEventRecord(e1, b->stream), "steps_batch_run: autotuner") ||
+                    !cuda_ok(cudaEventSynchronize(e1), "steps_batch_run: autotuner") ||
+                    !cuda_ok(cudaEventElapsedTime(&ms, e0, e1), "steps_batch_run: autotuner")) {
+                    if (rc == STEPS_OK) rc = STEPS_ERR_CUDA;
+                    break;
+                }
+                total[c] += ms;
+                done += 1;
             }
-            b->tune_ms[c] = ms / 3.f;
-            if (ms < best) {
-                best = ms;
-                best_b = cand[c];
-            }
-            done += 4;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (rc) return rc;
+        int best_b = 256;
+        float best = total[1];
+        for (int c = 0; c < 3; ++c) {
+            b->tune_ms[c] = total[c] / 2.f;
+            if (total[c] < 0.98f * best) {
+                best = total[c];
+                best_b = cand[c];
+            }
+        }
         b->block = best_b;
         b->autotune = false;
     }
