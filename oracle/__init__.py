@@ -6,9 +6,10 @@ and its Python binding) never imports it.
 
 ``OracleSim`` wraps ``steps_oracle.c`` (plain serial C, FP64), built by
 ``oracle.build.build()`` with gcc and no floating-point contraction.
-``prec=64`` takes every reaction decision in double precision (the method's
-definition); ``prec=32`` takes them with the float operations the CUDA
-kernel uses, so that the two can be compared element by element.
+``prec=64`` takes every reaction decision in double precision with 53-bit
+uniforms (the method's definition); ``prec=32`` takes them with the float
+operations and 24-bit uniforms the CUDA kernel uses, so that the two can be
+compared element by element.
 """
 from __future__ import annotations
 

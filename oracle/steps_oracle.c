@@ -117,6 +117,13 @@ static void draw4_bulk(uint64_t seed, uint64_t window, uint32_t tet, int sp, uin
 /* Uniform in (0, 1] from the top 24 bits of a word: exact in float and double. */
 static double unit24(uint32_t w) { return (double)((w >> 8) + 1u) * (1.0 / 16777216.0); }
 
+/* Uniform in (0, 1] with 53 bits from two words: exact in double. */
+static double unit53(uint32_t hi, uint32_t lo)
+{
+    uint64_t x = (((uint64_t)hi << 32) | lo) >> 11;
+    return (double)(x + 1u) * (1.0 / 9007199254740992.0);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Natural logarithm in float arithmetic for the kernel-precision mode.     */
 /* Classical atanh series: x = 2^e f with f in (sqrt(1/2), sqrt(2)],        */
@@ -487,10 +494,10 @@ static void reaction_phase(const orc_sim *s, int64_t i, double tau_k, double inv
             for (int r = 0; r < s->R; ++r) { a[r] = active[r] ? prop64(s, r, N, nav) : 0.0; a0 += a[r]; }
             if (!(a0 > 0.0)) break;
             draw4(s->seed, s->k_total, (uint32_t)i, j++, ORC_PURPOSE_REAC, w);
-            double dt = -log(unit24(w[0])) / a0;
+            double dt = -log(unit53(w[0], w[1])) / a0;
             dt_new = dt_acc + dt;
             if (dt_new > tau_k) break;
-            double target = unit24(w[1]) * a0, c = 0.0;
+            double target = unit53(w[2], w[3]) * a0, c = 0.0;
             for (int r = 0; r < s->R; ++r) {
                 c += a[r];
                 if (c > target) { pick = r; break; }
