@@ -381,6 +381,14 @@ const char *steps_last_error(void);
 int steps_debug_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out);
 /* The step kernel's float natural logarithm on the device, n values. */
 int steps_debug_logf(const float *x, int64_t n, float *out);
+/* The step kernel's bounded wait for its bulk copies, on its own (a test of
+ * the failure path). One thread arms a barrier for a 16-byte copy: with
+ * deliver != 0 it issues the copy and the wait completes (STEPS_OK); with
+ * deliver = 0 nothing completes it, and the wait gives up after limit_cycles
+ * clock cycles (STEPS_ERR_TIMEOUT). No copy is in flight when the kernel
+ * ends, so the device stays usable. limit_cycles: 1 .. 2^31 (about a second
+ * at most); else STEPS_ERR_ARG. */
+int steps_debug_wait(int32_t deliver, int64_t limit_cycles);
 /* The host-side set-up of steps_sim_create alone, with no device work (for
  * tests of the host logic without a GPU): *tau (§2.1), the cumulative face
  * thresholds of every tet at the full window ([nt*4] uint32, 2^31 fixed

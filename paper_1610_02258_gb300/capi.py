@@ -34,7 +34,7 @@ EXPORTS = [
     "steps_sim_specialized", "steps_batch_specialized", "steps_sim_shape",
     "steps_server_options_default", "steps_server_create", "steps_server_destroy", "steps_server_submit",
     "steps_server_step", "steps_server_job_state", "steps_server_take_result", "steps_server_stats",
-    "steps_debug_host_tables",
+    "steps_debug_host_tables", "steps_debug_wait",
 ]
 
 
@@ -86,6 +86,7 @@ def _load():
         "steps_last_error": (ctypes.c_char_p, []),
         "steps_debug_philox": (ctypes.c_int, [u64, P, i64, P]),
         "steps_debug_logf": (ctypes.c_int, [P, i64, P]),
+        "steps_debug_wait": (ctypes.c_int, [ctypes.c_int32, i64]),
         "steps_run_noalloc": (ctypes.c_int, [P, P, ctypes.c_double]),
         "steps_batch_options_default": (None, [ctypes.POINTER(steps_batch_options)]),
         "steps_batch_create": (ctypes.c_int, [P, i32, ctypes.POINTER(steps_batch_options), P, PP]),
@@ -300,6 +301,12 @@ def steps_debug_logf(x):
     out = np.empty_like(a)
     _check(lib.steps_debug_logf(_ptr(a), a.size, _ptr(out)))
     return out
+
+
+def steps_debug_wait(deliver, limit_cycles):
+    """The step kernel's bounded bulk-copy wait on its own: raises StepsError
+    (code -6, STEPS_ERR_TIMEOUT) when the wait ran out."""
+    _check(lib.steps_debug_wait(1 if deliver else 0, int(limit_cycles)))
 
 
 def steps_batch_options_default():

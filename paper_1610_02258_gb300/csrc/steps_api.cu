@@ -852,6 +852,37 @@ int steps_debug_host_tables(const steps_mesh *mesh, const steps_model *model, in
     return STEPS_OK;
 }
 
+int steps_debug_wait(int32_t deliver, int64_t limit_cycles) {
+    if (limit_cycles < 1 || limit_cycles > (int64_t)1 << 31) {
+        set_error("steps_debug_wait: limit_cycles must be in [1, 2^31]");
+        return STEPS_ERR_ARG;
+    }
+    void *src = nullptr;
+    uint32_t *status = nullptr;
+    int rc = STEPS_OK;
+    if (!cuda_ok(cudaMalloc(&src, 16), "steps_debug_wait: alloc") ||
+        !cuda_ok(cudaMalloc((void **)&status, 4), "steps_debug_wait: alloc"))
+        rc = STEPS_ERR_OOM;
+    uint32_t st = 0;
+    if (!rc && (!cuda_ok(cudaMemset(src, 0, 16), "steps_debug_wait") ||
+                !cuda_ok(cudaMemset(status, 0xFF, 4), "steps_debug_wait")))
+        rc = STEPS_ERR_CUDA;
+    if (!rc) rc = launch_wait_test(src, deliver != 0, (long long)limit_cycles, status, nullptr);
+    if (!rc && !cuda_ok(cudaMemcpy(&st, status, 4, cudaMemcpyDeviceToHost), "steps_debug_wait")) rc = STEPS_ERR_CUDA;
+    cudaFree(src);
+    cudaFree(status);
+    if (rc) return rc;
+    if (st == 4u) {
+        set_error("steps_debug_wait: the bulk-copy wait did not complete within its limit");
+        return STEPS_ERR_TIMEOUT;
+    }
+    if (st != 0u) {
+        set_error("steps_debug_wait: unexpected status");
+        return STEPS_ERR_STATE;
+    }
+    return STEPS_OK;
+}
+
 int steps_debug_logf(const float *x, int64_t n, float *out) {
     CHECK_NULL(x, "steps_debug_logf");
     CHECK_NULL(out, "steps_debug_logf");

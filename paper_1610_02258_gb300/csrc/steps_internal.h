@@ -59,6 +59,7 @@ int prefetch_distance(const void *kernel, int block, size_t smem);
 int launch_step(const ModelDev &m, const StepArgs &a, int block, void *stream);
 int launch_philox_test(uint64_t seed, const uint32_t *d_ctr, int64_t n, uint32_t *d_out, void *stream);
 int launch_logf_test(const float *d_x, int64_t n, float *d_out, void *stream);
+int launch_wait_test(const void *d_src, int deliver, long long limit, uint32_t *d_status, void *stream);
 int launch_add_u64(uint64_t *p, uint64_t v, void *stream);
 int launch_step_batch(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R,
                       bool any_order0, int block, void *stream);

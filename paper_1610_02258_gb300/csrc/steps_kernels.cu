@@ -27,6 +27,21 @@ __global__ void logf_test_kernel(const float *x, int64_t n, float *out) {
     out[i] = steps_logf(x[i]);
 }
 
+// The step kernel's bounded wait on its own: one thread arms an mbarrier for
+// a 16-byte bulk copy. With `deliver` it issues the copy and the wait
+// completes; without, nothing completes the phase and the wait gives up
+// after `limit` cycles. No copy is left in flight when the block exits.
+// status: 0 completed, 4 timed out (the step kernel's error bit).
+__global__ void wait_test_kernel(const uint4 *src, int deliver, long long limit, uint32_t *status) {
+    __shared__ __align__(16) uint4 buf;
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, 16u);
+    if (deliver) bulk_g2s(&buf, src, 16u, &bar);
+    *status = mbar_wait_bounded(&bar, 0, limit) ? 0u : 4u;
+}
+
 __global__ void add_u64_kernel(uint64_t *p, uint64_t v) { *p += v; }
 
 template <int BLOCK, int RM, bool Z>
@@ -125,6 +140,11 @@ int launch_philox_test(uint64_t seed, const uint32_t *d_ctr, int64_t n, uint32_t
     if (n <= 0) return STEPS_OK;
     philox_test_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
         (uint32_t)seed, (uint32_t)(seed >> 32), (const uint4 *)d_ctr, n, (uint4 *)d_out);
+    return cudaGetLastError() == cudaSuccess ? STEPS_OK : STEPS_ERR_CUDA;
+}
+
+int launch_wait_test(const void *d_src, int deliver, long long limit, uint32_t *d_status, void *stream) {
+    wait_test_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((const uint4 *)d_src, deliver, limit, d_status);
     return cudaGetLastError() == cudaSuccess ? STEPS_OK : STEPS_ERR_CUDA;
 }
 

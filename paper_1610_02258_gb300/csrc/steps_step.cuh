@@ -86,12 +86,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Waits for the phase with the given parity to complete, for at most about
-// 2^30 clock cycles (~0.5 s); returns false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// Waits for the phase with the given parity to complete, for at most `limit`
+// clock cycles (by default 2^30, ~0.5 s); returns false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit = 1ll << 30) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1ll << 30)) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
