@@ -685,7 +685,7 @@ def run_ours(args):
                          "batched": measure_batched(args, capi, I, torch, peak) if args.batch_replicates > 0 else None,
                          "served": measure_served(args, capi, I) if args.served_jobs > 0 else None}
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_windows, max(5, args.cpu_windows // 4))
+        line["cpu_baseline"] = cpu_baseline(w, 4 * args.cpu_windows, max(5, args.cpu_windows // 4))
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
