@@ -21,6 +21,7 @@ import numpy as np
 from .build import LIB_PATH, build
 
 OCC, END = 1, 0
+EULER, EXP = 0, 1  # leave laws: p = tau d (default) or p = 1 - exp(-tau d)
 _lib = None
 
 
@@ -61,6 +62,8 @@ def lib():
         L.orc_get_cumg.argtypes = [P, P]
         L.orc_get_species_thresholds.argtypes = [P, ctypes.c_int, ctypes.c_double, P]
         L.orc_get_species_thresholds.restype = c_u32
+        L.orc_set_leave_law.argtypes = [P, ctypes.c_int]
+        L.orc_set_leave_law.restype = ctypes.c_int
         L.orc_geometry.argtypes = [c_i64, P, c_i64, P, P, P, P, P, P]
         L.orc_geometry.restype = ctypes.c_int
         L.orc_adjacency.argtypes = [c_i64, c_i64, P, P]
@@ -148,7 +151,7 @@ def sample_bulk(seed, window, tet, species, M, T):
 class OracleSim:
     """Serial reference simulation. Counts are [S, nt] in the caller's tet order."""
 
-    def __init__(self, verts, tets, model, seed: int, occ: int = OCC, prec: int = 64):
+    def __init__(self, verts, tets, model, seed: int, occ: int = OCC, prec: int = 64, leave: int = EULER):
         self._verts = np.ascontiguousarray(verts, np.float64)
         self._tets = np.ascontiguousarray(tets, np.int32)
         self.S = model.n_species
@@ -168,6 +171,8 @@ class OracleSim:
                                    ctypes.c_uint64(seed), occ, prec, ctypes.byref(err))
         if not self._h:
             raise ValueError(f"oracle create failed ({err.value})")
+        if leave != EULER and lib().orc_set_leave_law(self._h, int(leave)) != 0:
+            raise ValueError("oracle: bad leave law or out of memory")
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -250,8 +255,8 @@ class OracleSim:
         return out, int(scale)
 
 
-def from_workload(w, occ: int = OCC, prec: int = 64, seed=None) -> OracleSim:
-    sim = OracleSim(w.verts, w.tets, w.model, w.seed if seed is None else seed, occ=occ, prec=prec)
+def from_workload(w, occ: int = OCC, prec: int = 64, seed=None, leave: int = EULER) -> OracleSim:
+    sim = OracleSim(w.verts, w.tets, w.model, w.seed if seed is None else seed, occ=occ, prec=prec, leave=leave)
     sim.set_counts(w.counts)
     for r, m in w.reac_masks.items():
         sim.set_reac_mask(r, m)

@@ -28,7 +28,10 @@
  *     d_f the distance between the two tets' barycentres; boundary faces are
  *     reflective. tau is the min over diffusive species only.
  *   - binomial(Nbar, tau, d) is Bin(M, p) with p = tau * d_{S,tet} (p <= 1 by
- *     the choice of tau) and M an integer trial count: M = N_S for a species no
+ *     the choice of tau; the EULER law, the default) or, as an option, with
+ *     p = 1 - exp(-tau d_{S,tet}) (the EXP law: the probability that an
+ *     exponential leaving time with rate d falls inside the window), and M an
+ *     integer trial count: M = N_S for a species no
  *     reaction changed in the window; otherwise the occupancy integral is
  *     closed at tau and Nbar is rounded stochastically (floor + Bernoulli of
  *     the fraction) and clamped to the end-of-window count (mode OCC). Mode END
@@ -293,6 +296,8 @@ typedef struct {
     double *g;         /* [nt*4] */
     double *cumg;      /* [nt*4] cumulative g over local faces */
     uint32_t *thr;     /* [nt*4] fixed-point cumulative thresholds at the full window */
+    int leave_exp;     /* 1 = EXP leave law; thresholds from share and exp_leave() */
+    uint32_t *share;   /* [nt*4] floor(2^31 cumg_f / G), EXP law only */
     double tau, dmax, gmax;
     int32_t *cnt;      /* [S*nt] current counts */
     int32_t *nxt;      /* [S*nt] */
@@ -342,7 +347,7 @@ static void setup_rates(orc_sim *s)
 void orc_destroy(orc_sim *s)
 {
     if (!s) return;
-    free(s->nbr); free(s->vol); free(s->g); free(s->cumg); free(s->thr);
+    free(s->nbr); free(s->vol); free(s->g); free(s->cumg); free(s->thr); free(s->share);
     free(s->cnt); free(s->nxt); free(s->mask);
     free(s->rev); free(s->mv);
     free(s);
@@ -622,21 +627,61 @@ static uint32_t species_scale(const orc_sim *s, int sp, double tau_k)
     return (uint32_t)fl;
 }
 
-/* Cumulative face thresholds of species sp in tet i for a window whose
- * species scale is `scale`: T_f = (A_{i,f} * R_S) >> 31. */
-static void species_thresholds(const orc_sim *s, int64_t i, uint32_t scale, uint32_t T[4])
+/* EXP law: L = floor(2^31 (1 - exp(-(tau_k D_S) G_tet))), clamped to
+ * [0, 2^31]; 0 for an immobile species. */
+static uint32_t exp_leave(const orc_sim *s, int64_t i, int sp, double tau_k)
 {
+    if (!(s->D[sp] > 0.0) || !isfinite(s->tau)) return 0;
+    double x = (tau_k * s->D[sp]) * s->cumg[4 * i + 3];
+    double fl = floor((1.0 - exp(-x)) * 2147483648.0);
+    if (fl < 0.0) fl = 0.0;
+    if (fl > 2147483648.0) fl = 2147483648.0;
+    return (uint32_t)fl;
+}
+
+/* Cumulative face thresholds of species sp in tet i for a window of length
+ * tau_k whose species scale is `scale`: EULER T_f = (A_{i,f} * R_S) >> 31;
+ * EXP T_f = (share_{i,f} * L_{S,i}) >> 31. */
+static void species_thresholds(const orc_sim *s, int64_t i, int sp, double tau_k, uint32_t scale, uint32_t T[4])
+{
+    if (s->leave_exp) {
+        uint32_t L = exp_leave(s, i, sp, tau_k);
+        for (int f = 0; f < 4; ++f)
+            T[f] = (uint32_t)(((uint64_t)s->share[4 * i + f] * (uint64_t)L) >> 31);
+        return;
+    }
     for (int f = 0; f < 4; ++f)
         T[f] = (uint32_t)(((uint64_t)s->thr[4 * i + f] * (uint64_t)scale) >> 31);
 }
 
 /* The thresholds every tet uses for species sp in a window of length tau_k
- * ([nt*4]), and the species scale R_S as the return value. */
+ * ([nt*4]), and the species scale R_S as the return value (EULER law). */
 uint32_t orc_get_species_thresholds(const orc_sim *s, int sp, double tau_k, uint32_t *out)
 {
     uint32_t scale = species_scale(s, sp, tau_k);
-    for (int64_t i = 0; i < s->nt; ++i) species_thresholds(s, i, scale, out + 4 * i);
+    for (int64_t i = 0; i < s->nt; ++i) species_thresholds(s, i, sp, tau_k, scale, out + 4 * i);
     return scale;
+}
+
+/* Leave law: 0 = EULER (p = tau d, default), 1 = EXP (p = 1 - exp(-tau d)). */
+int orc_set_leave_law(orc_sim *s, int exp_law)
+{
+    if (exp_law != 0 && exp_law != 1) return ORC_ERR_ARG;
+    if (exp_law && !s->share) {
+        s->share = (uint32_t *)malloc(sizeof(uint32_t) * 4 * s->nt);
+        if (!s->share) return ORC_ERR_OOM;
+        for (int64_t i = 0; i < s->nt; ++i) {
+            double G = s->cumg[4 * i + 3];
+            for (int f = 0; f < 4; ++f) {
+                double fl = G > 0.0 ? floor((s->cumg[4 * i + f] / G) * 2147483648.0) : 0.0;
+                if (fl < 0.0) fl = 0.0;
+                if (fl > 2147483648.0) fl = 2147483648.0;
+                s->share[4 * i + f] = (uint32_t)fl;
+            }
+        }
+    }
+    s->leave_exp = exp_law;
+    return ORC_OK;
 }
 
 /* One diffusion window of length tau_k over all tets (Algorithm 1). */
@@ -660,7 +705,7 @@ static void window(orc_sim *s, double tau_k)
             int32_t leave[4] = {0, 0, 0, 0};
             if (s->D[sp] > 0.0) {
                 uint32_t T[4];
-                species_thresholds(s, i, scale[sp], T);
+                species_thresholds(s, i, sp, tau_k, scale[sp], T);
                 sample_species(s, i, sp, M[sp], T, &w, leave);
             }
             int32_t n = leave[0] + leave[1] + leave[2] + leave[3];
@@ -728,7 +773,7 @@ static void par_tet_pass1(orc_par_job *job, int64_t i, int64_t *events)
         int32_t leave[4] = {0, 0, 0, 0};
         if (s->D[sp] > 0.0) {
             uint32_t T[4];
-            species_thresholds(s, i, job->scale[sp], T);
+            species_thresholds(s, i, sp, job->tau_k, job->scale[sp], T);
             sample_species(s, i, sp, M[sp], T, &w, leave);
         }
         int32_t n = leave[0] + leave[1] + leave[2] + leave[3];

@@ -19,6 +19,9 @@ d_{S,tet} = sum_f D_S A_f / (V d_f)).
   A -> B event is clamped back to the end count), which costs half a trial on
   average. So E[M_OCC - M_END] / tau -> -kb N_B / 2, and the trial counts of
   the two modes agree in every tet where no reaction fired.
+- The EXP leave law (p = 1 - exp(-tau_k d) instead of tau_k d): counts follow
+  I + diag((1 - e^{-tau_k d}) / d) D Q and not the EULER matrix, and its
+  thresholds lie within 3 units of 2^31 (1 - e^{-tau_k D G}) cumg_f / G.
 """
 import math
 
@@ -192,3 +195,75 @@ def test_occupancy_trials_approach_end_count():
         deltas.append((tau, d.mean()))
     (t1, d1), (t2, d2) = deltas
     assert d2 / d1 == pytest.approx(t2 / t1, rel=0.35)
+
+
+def exp_window_matrix(nbr, g, tau_k, D):
+    """EXP law: molecule in tet i leaves with 1 - exp(-tau_k d_i), d_i = D G_i,
+    through face f in proportion to g_f: P = I + diag((1 - e^{-tau_k d}) / d) D Q."""
+    nt = len(nbr)
+    G = g.sum(axis=1)
+    P = np.zeros((nt, nt))
+    for i in range(nt):
+        if G[i] <= 0:
+            P[i, i] = 1.0
+            continue
+        p_leave = 1.0 - np.exp(-tau_k * D * G[i])
+        for f in range(4):
+            if nbr[i, f] >= 0:
+                P[i, nbr[i, f]] += p_leave * g[i, f] / G[i]
+        P[i, i] = 1.0 - P[i].sum()
+    return P
+
+
+@pytest.mark.parametrize("c", [1.0, 0.6])
+def test_exp_law_diffusion_is_multinomial(c):
+    """The EXP leave law (p = 1 - exp(-tau d)): per-tet totals over 400
+    copies after K windows of c*tau are Multinomial with a row of the EXP
+    matrix's K-th power, and not with the EULER law's (p = tau d)."""
+    bv, bt = I.kuhn_box_mesh(3, 3, 2, H)
+    bv = I.jitter_box_vertices(bv, H, 0.2, seed=8)
+    copies, N0, K, D = 400, 40, 3, 1e-11
+    verts, tets = I.replicate_mesh(bv, bt, copies, spacing=3 * H + 4 * H)
+    nt0 = len(bt)
+    m = I.model_from_lists(["A"], [D], [])
+    start = 17
+    cnt = np.zeros((1, nt0 * copies), np.int32)
+    cnt[0, start::nt0] = N0
+    sim = oracle.OracleSim(verts, tets, m, seed=61, leave=oracle.EXP)
+    sim.set_counts(cnt)
+    for _ in range(K):
+        sim.step(c * sim.tau)
+    agg = sim.get_counts()[0].reshape(copies, nt0).sum(axis=0)
+    assert agg.sum() == N0 * copies
+    nbr, vol, g = np_geometry(bv, bt)
+    tau = 1.0 / (D * g.sum(axis=1).max())
+    law = np.linalg.matrix_power(exp_window_matrix(nbr, g, c * tau, D), K)[start]
+    assert chi2_table_pvalue(agg, law) > 1e-3
+    euler = np.linalg.matrix_power(one_window_matrix(nbr, g, c * tau * D), K)[start]
+    assert chi2_table_pvalue(agg, euler) < 1e-6
+
+
+@pytest.mark.parametrize("c", [1.0, 0.37])
+def test_exp_thresholds_against_fp64(c):
+    """EXP law thresholds T_f = (share_f * L) >> 31 lie below
+    2^31 (1 - exp(-tau_k D_S G)) cumg_f / G by less than 3 units (two floors
+    of factors <= 1, and the product's floor)."""
+    bv, bt = I.kuhn_box_mesh(6, 5, 4, H)
+    verts = I.jitter_box_vertices(bv, H, 0.2, seed=12)
+    D = np.array([1e-11, 3.7e-12, 0.0, 2.2e-13])
+    m = I.model_from_lists([f"S{s}" for s in range(len(D))], D, [])
+    sim = oracle.OracleSim(verts, bt, m, seed=1, leave=oracle.EXP)
+    nbr, vol, g = np_geometry(verts, bt)
+    cumg = np.cumsum(g, axis=1)
+    G = cumg[:, 3:4]
+    tau = 1.0 / (D.max() * G.max())
+    tau_k = c * tau
+    for s, Ds in enumerate(D):
+        T, _ = sim.species_thresholds(s, tau_k)
+        if Ds == 0.0:
+            assert not T.any()
+            continue
+        X = 2.0**31 * (1.0 - np.exp(-tau_k * Ds * G)) * cumg / G
+        gap = X - T.astype(np.float64)
+        assert gap.min() >= -1e-5 and gap.max() < 3.0
+        assert np.all(np.diff(T.astype(np.int64), axis=1) >= 0)
