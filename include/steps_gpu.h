@@ -56,6 +56,11 @@ typedef struct steps_sim steps_sim;
 #define STEPS_OCC_MEAN 1 /* Algorithm 1: mean occupancy Nbar = O_S / tau, stochastically rounded (default) */
 #define STEPS_OCC_END 0  /* end-of-reaction-phase count */
 
+/* Leave law of the diffusion operator's binomial(Nbar, tau, d). */
+#define STEPS_LEAVE_EULER 0 /* p = tau d (the default) */
+#define STEPS_LEAVE_EXP 1   /* p = 1 - exp(-tau d): an exponential leaving time of rate d inside the window; runs on
+                               the model-specialised kernel only (specialize 0 or 1; creation forces it) */
+
 /* Internal tet order. */
 #define STEPS_REORDER_NONE 0
 #define STEPS_REORDER_MORTON 1 /* Morton (Z-order) of barycentres (default) */
@@ -68,7 +73,8 @@ typedef struct steps_options {
     int32_t specialize;  /* step kernel compiled for this model at run time (NVRTC): 0 = when the mesh has at
                             least 65,536 tets and NVRTC is available (default), 1 = always (sim creation fails
                             with STEPS_ERR_CUDA if it cannot be built), -1 = never (the generic kernel) */
-    int32_t reserved[3]; /* set to 0 */
+    int32_t leave_law;   /* STEPS_LEAVE_EULER (default) or STEPS_LEAVE_EXP */
+    int32_t reserved[2]; /* set to 0 */
 } steps_options;
 
 /* Fill *opt with the defaults. */

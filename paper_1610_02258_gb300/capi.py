@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libsteps_gpu.so")
 
 STEPS_OCC_MEAN, STEPS_OCC_END = 1, 0
 STEPS_REORDER_NONE, STEPS_REORDER_MORTON = 0, 1
+STEPS_LEAVE_EULER, STEPS_LEAVE_EXP = 0, 1
 
 ERRORS = {-1: "STEPS_ERR_ARG", -2: "STEPS_ERR_MESH", -3: "STEPS_ERR_MODEL", -4: "STEPS_ERR_OOM",
           -5: "STEPS_ERR_CUDA", -6: "STEPS_ERR_TIMEOUT", -7: "STEPS_ERR_STATE"}
@@ -46,7 +47,8 @@ class StepsError(RuntimeError):
 
 class steps_options(ctypes.Structure):
     _fields_ = [("occupancy", ctypes.c_int32), ("reorder", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("specialize", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("use_graph", ctypes.c_int32), ("specialize", ctypes.c_int32), ("leave_law", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class steps_batch_options(ctypes.Structure):
@@ -442,7 +444,7 @@ class Simulation:
     the calls above; counts are [S, nt] numpy arrays in the caller's tet order)."""
 
     def __init__(self, verts, tets, model, seed, occupancy=STEPS_OCC_MEAN, reorder=STEPS_REORDER_MORTON,
-                 block=256, use_graph=True, cuda_stream=None, specialize=0):
+                 block=256, use_graph=True, cuda_stream=None, specialize=0, leave_law=0):
         self.S = model.n_species
         self.R = model.n_reac
         self.nt = int(np.asarray(tets).shape[0])
@@ -454,6 +456,7 @@ class Simulation:
         opt.block = block
         opt.use_graph = 1 if use_graph else 0
         opt.specialize = int(specialize)
+        opt.leave_law = int(leave_law)
         self._sim = steps_sim_create(self._mesh, self._model, seed, opt, cuda_stream)
 
     def clone(self, seed, cuda_stream=None):

@@ -97,6 +97,7 @@ struct steps_sim {
     size_t rec_bytes = 0;
     void *spec = nullptr;           // step kernel compiled for this model (cached process-wide), or null
     int32_t *d_trial = nullptr;     // [S][Tpad] trial counts for specialised kernels that keep them in global memory
+    uint32_t *d_leave[2] = {nullptr, nullptr};  // EXP leave law: [S][Tpad] tables of the full and the last window
     std::string spec_why;           // why there is none
     // time
     double t_base = 0.0;
@@ -125,6 +126,26 @@ struct steps_sim {
         cudaFree(d_stage);
         cudaFree(d_rec);
         cudaFree(d_trial);
+        cudaFree(d_leave[0]);
+        cudaFree(d_leave[1]);
+    }
+
+    // EXP leave law: the table of a window of length tau_k, into the full
+    // window's buffer (tau_k == tau) or the last window's, in stream order
+    // (the host copy is staged before the call returns)
+    int upload_leave(double tau_k, cudaStream_t st) {
+        if (!d_leave[0]) return STEPS_OK;
+        std::vector<uint32_t> h;
+        try {
+            exp_leave_table(model, tab, tau_k, (size_t)Tpad, h);
+        } catch (const std::bad_alloc &) {
+            set_error("leave table: out of host memory");
+            return STEPS_ERR_OOM;
+        }
+        uint32_t *dst = tau_k == tab.tau ? d_leave[0] : d_leave[1];
+        return cuda_ok(cudaMemcpyAsync(dst, h.data(), h.size() * 4, cudaMemcpyHostToDevice, st), "leave table upload")
+                   ? STEPS_OK
+                   : STEPS_ERR_CUDA;
     }
 
     // the global trial buffer the model-specialised kernels of this model need (if any)
@@ -167,6 +188,7 @@ struct steps_sim {
         a.occ = opt.occupancy;
         a.prefetch = 1;  // the launch sets the distance: half a resident wave
         a.trial = d_trial;
+        a.leave = d_leave[0] ? (tau_k == tab.tau ? d_leave[0] : d_leave[1]) : nullptr;
         std::memcpy(a.scale, scale, sizeof(a.scale));
         return a;
     }
@@ -179,6 +201,10 @@ struct steps_sim {
     int window_launch(double tau_k) {  // one window of explicit length, plain launch
         uint32_t scale[kMaxSpecies] = {};
         for (int s = 0; s < S; ++s) scale[s] = species_scale(model, tab, s, tau_k);
+        if (tau_k != tab.tau) {
+            int rc = upload_leave(tau_k, stream);
+            if (rc) return rc;
+        }
         StepArgs a = args(cur, k_total, nullptr, tau_k, scale);
         int rc = launch(a, stream);
         if (rc) return rc;
@@ -332,10 +358,23 @@ int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t 
             set_error("steps_sim_create: bad occupancy mode");
             return STEPS_ERR_ARG;
         }
+        if (s->opt.leave_law != STEPS_LEAVE_EULER && s->opt.leave_law != STEPS_LEAVE_EXP) {
+            set_error("steps_sim_create: bad leave law");
+            return STEPS_ERR_ARG;
+        }
+        if (s->opt.leave_law == STEPS_LEAVE_EXP) {
+            if (s->opt.specialize < 0) {
+                set_error("steps_sim_create: the EXP leave law runs on the model-specialised kernel only "
+                          "(specialize must be 0 or 1)");
+                return STEPS_ERR_ARG;
+            }
+            s->opt.specialize = 1;
+        }
     } else {
         steps_options_default(&s->opt);
     }
     s->model = model->m;
+    s->model.leave_exp = s->opt.leave_law == STEPS_LEAVE_EXP;
     s->stream = (cudaStream_t)cuda_stream;
     if (!cuda_ok(cudaGetDevice(&s->device), "steps_sim_create: cudaGetDevice")) return STEPS_ERR_CUDA;
     s->T = mesh->m.nt;
@@ -371,6 +410,10 @@ int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t 
         alloc((void **)&s->d_orig, Tpad * 4);
         alloc((void **)&s->d_inv_perm, T * 4);
     }
+    if (s->model.leave_exp) {
+        alloc((void **)&s->d_leave[0], S * Tpad * 4);
+        alloc((void **)&s->d_leave[1], S * Tpad * 4);
+    }
     if (e != cudaSuccess) {
         set_error(std::string("steps_sim_create: device allocation failed: ") + cudaGetErrorString(e));
         cudaGetLastError();
@@ -391,6 +434,10 @@ int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t 
              cuda_ok(cudaMemcpy(s->d_orig, s->tab.perm.data(), T * 4, cudaMemcpyHostToDevice), "upload perm") &&
              cuda_ok(cudaMemcpy(s->d_inv_perm, s->tab.inv_perm.data(), T * 4, cudaMemcpyHostToDevice),
                      "upload inv_perm");
+    if (ok && s->model.leave_exp) {
+        ok = s->upload_leave(s->tab.tau, s->stream) == STEPS_OK &&
+             cuda_ok(cudaStreamSynchronize(s->stream), "leave table upload");
+    }
     if (!ok) return STEPS_ERR_CUDA;
     // the model-specialised step kernel (compiled once per model and block size)
     constexpr int64_t kSpecializeMinTets = 65536;
@@ -452,6 +499,10 @@ int steps_sim_clone(const steps_sim *src, uint64_t seed, void *cuda_stream, step
     }
     if (src->d_rmask) alloc((void **)&s->d_rmask, Tpad * 4);
     if (src->d_trial) alloc((void **)&s->d_trial, S * Tpad * 4);
+    if (src->d_leave[0]) {
+        alloc((void **)&s->d_leave[0], S * Tpad * 4);
+        alloc((void **)&s->d_leave[1], S * Tpad * 4);
+    }
     if (e != cudaSuccess) {
         set_error(std::string("steps_sim_clone: device allocation failed: ") + cudaGetErrorString(e));
         cudaGetLastError();
@@ -470,6 +521,9 @@ int steps_sim_clone(const steps_sim *src, uint64_t seed, void *cuda_stream, step
              cuda_ok(cudaMemcpyAsync(s->d_inv_perm, src->d_inv_perm, T * 4, cudaMemcpyDeviceToDevice, st), "clone");
     if (ok && src->d_rmask)
         ok = cuda_ok(cudaMemcpyAsync(s->d_rmask, src->d_rmask, Tpad * 4, cudaMemcpyDeviceToDevice, st), "clone");
+    if (ok && src->d_leave[0])
+        ok = cuda_ok(cudaMemcpyAsync(s->d_leave[0], src->d_leave[0], S * Tpad * 4, cudaMemcpyDeviceToDevice, st),
+                     "clone");
     if (!ok || !cuda_ok(cudaStreamSynchronize(st), "steps_sim_clone")) return STEPS_ERR_CUDA;
     *out = s.release();
     return STEPS_OK;
@@ -480,7 +534,7 @@ int steps_sim_device_bytes(const steps_sim *sim, int64_t *bytes) {
     CHECK_NULL(bytes, "steps_sim_device_bytes");
     const int64_t Tpad = sim->Tpad, S = sim->S, T = sim->T;
     *bytes = 2 * S * Tpad * 4 + Tpad * 16 * 2 + Tpad * 4 + 16 + S * T * 4 + (sim->d_orig ? Tpad * 4 + T * 4 : 0) +
-             (sim->d_trial ? S * Tpad * 4 : 0) +
+             (sim->d_trial ? S * Tpad * 4 : 0) + (sim->d_leave[0] ? 2 * S * Tpad * 4 : 0) +
              (sim->d_rmask ? Tpad * 4 : 0);
     return STEPS_OK;
 }
@@ -1097,8 +1151,15 @@ int steps_batch_create(steps_sim *const *members, int32_t n, const steps_batch_o
         return STEPS_ERR_ARG;
     }
     constexpr int64_t kSpecializeMinTets = 65536;
-    b->spec_forced = o.specialize > 0;
-    b->use_spec = uniform && (o.specialize > 0 || (o.specialize == 0 && tets >= kSpecializeMinTets));
+    bool any_exp = false;
+    for (int32_t j = 0; j < n; ++j) any_exp = any_exp || members[j]->model.leave_exp;
+    if (any_exp && (!uniform || o.specialize < 0)) {
+        set_error("steps_batch_create: members with the EXP leave law run on the model-specialised batched "
+                  "kernel only: they need one model structure and specialize 0 or 1");
+        return STEPS_ERR_ARG;
+    }
+    b->spec_forced = o.specialize > 0 || any_exp;
+    b->use_spec = uniform && (o.specialize > 0 || any_exp || (o.specialize == 0 && tets >= kSpecializeMinTets));
     if (b->use_spec)
         for (steps_sim *m : b->members) {
             int rc = m->ensure_trial();
@@ -1248,6 +1309,10 @@ int batch_enqueue(steps_batch *b, const double *t_end) {
             any_partial = true;
             uint32_t scale[kMaxSpecies] = {};
             for (int s = 0; s < m->S; ++s) scale[s] = species_scale(m->model, m->tab, s, partial[j]);
+            if (partial[j] != m->tab.tau) {
+                int rl = m->upload_leave(partial[j], b->stream);  // after the full windows, in stream order
+                if (rl) return rl;
+            }
             StepArgs a = m->args(0, w, nullptr, partial[j], scale);
             a.err = b->d_err;
             e.args = a;
@@ -1391,6 +1456,11 @@ extern "C" int steps_run_noalloc(steps_sim *sim, int32_t *d_counts, double t_end
         return STEPS_ERR_ARG;
     }
     if (int rf = refuse_failed(sim, "steps_run_noalloc")) return rf;
+    if (sim->d_leave[0]) {
+        set_error("steps_run_noalloc: the EXP leave law needs a host-built table for a shortened window; "
+                  "use steps_run");
+        return STEPS_ERR_ARG;
+    }
     // the scratch address is per device, and the simulation's stream and
     // tables belong to the device it was created on
     int dev = -1;

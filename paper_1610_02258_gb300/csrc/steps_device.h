@@ -84,6 +84,7 @@ struct StepArgs {
     int32_t occ;                  // STEPS_OCC_*
     int32_t prefetch;             // tiles ahead whose tables a block prefetches into L2 (0 = none)
     int32_t *trial;               // [S][Tpad] trial counts, for kernels that keep them in global memory
+    const uint32_t *leave;        // [S][Tpad] EXP leave law: floor(2^31 (1 - exp(-tau_k D_S G_tet))), or nullptr
     uint32_t scale[kMaxSpecies];  // per-species fixed-point scale for this window length
 };
 

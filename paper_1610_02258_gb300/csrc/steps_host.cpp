@@ -275,23 +275,45 @@ void build_tables(const HostMesh &mesh, const HostModel &model, int reorder, Tab
     t.inv_perm.resize((size_t)nt);
     for (int64_t d = 0; d < nt; ++d) t.inv_perm[(size_t)t.perm[(size_t)d]] = (int32_t)d;
 
-    // fixed-point cumulative thresholds A_{i,f} = floor(2^31 tau Dmax cumg_{i,f})
+    // fixed-point cumulative thresholds: EULER A_{i,f} = floor(2^31 tau Dmax cumg_{i,f});
+    // EXP the face shares floor(2^31 cumg_{i,f} / G_i) (the leave probability is per
+    // species and tet, exp_leave_table)
     double pt = std::isfinite(t.tau) ? t.tau * t.dmax : 0.0;
     t.nbr_dev.resize((size_t)(4 * nt));
     t.thr_dev.resize((size_t)(4 * nt));
     t.inv_nav_dev.resize((size_t)nt);
+    t.G_dev.resize((size_t)nt);
     for (int64_t d = 0; d < nt; ++d) {
         int64_t i = t.perm[(size_t)d];
+        const double G = cumg[(size_t)(4 * i + 3)];
+        t.G_dev[(size_t)d] = G;
         for (int f = 0; f < 4; ++f) {
             int32_t j = mesh.nbr[(size_t)(4 * i + f)];
             t.nbr_dev[(size_t)(4 * d + f)] = j < 0 ? -1 : t.inv_perm[(size_t)j];
-            double x = (pt * cumg[(size_t)(4 * i + f)]) * 2147483648.0;
-            double fl = std::floor(x);
+            double fl;
+            if (model.leave_exp) fl = G > 0.0 ? std::floor((cumg[(size_t)(4 * i + f)] / G) * 2147483648.0) : 0.0;
+            else fl = std::floor((pt * cumg[(size_t)(4 * i + f)]) * 2147483648.0);
             fl = std::min(2147483648.0, std::max(0.0, fl));
             t.thr_dev[(size_t)(4 * d + f)] = (uint32_t)fl;
         }
         double nav = kAvogadro * (mesh.vol[(size_t)i] * 1000.0);
         t.inv_nav_dev[(size_t)d] = (float)(1.0 / nav);
+    }
+}
+
+void exp_leave_table(const HostModel &model, const Tables &t, double tau_k, size_t Tpad, std::vector<uint32_t> &out) {
+    const size_t T = t.G_dev.size();
+    out.assign((size_t)model.S * Tpad, 0u);
+    if (!std::isfinite(t.tau)) return;
+    for (int s = 0; s < model.S; ++s) {
+        const double D = model.D[(size_t)s];
+        if (!(D > 0.0)) continue;
+        for (size_t d = 0; d < T; ++d) {
+            const double x = (tau_k * D) * t.G_dev[d];
+            double fl = std::floor((1.0 - std::exp(-x)) * 2147483648.0);
+            fl = std::min(2147483648.0, std::max(0.0, fl));
+            out[(size_t)s * Tpad + d] = (uint32_t)fl;
+        }
     }
 }
 

@@ -33,6 +33,7 @@ struct HostModel {
     std::vector<int32_t> lhs, rhs;  // [R*S]
     std::vector<double> k;        // [R]
     ModelDev dev{};
+    bool leave_exp = false;       // the simulation's leave law is EXP (p = 1 - exp(-tau d))
 };
 
 // steps_host.cpp
@@ -47,9 +48,13 @@ struct Tables {
     std::vector<int32_t> nbr_dev;   // [T*4] device order, device indices
     std::vector<uint32_t> thr_dev;  // [T*4] device order
     std::vector<float> inv_nav_dev; // [T]
+    std::vector<double> G_dev;      // [T] device order: sum of the face rates g over internal faces
 };
 void build_tables(const HostMesh &mesh, const HostModel &model, int reorder, Tables &t);
 uint32_t species_scale(const HostModel &model, const Tables &t, int s, double tau_k);
+// EXP leave law: out[s * Tpad + d] = floor(2^31 (1 - exp(-(tau_k D_s) G_d))) for every
+// species and device-order tet (0 for immobile species and the padding).
+void exp_leave_table(const HostModel &model, const Tables &t, double tau_k, size_t Tpad, std::vector<uint32_t> &out);
 
 // steps_kernels.cu
 // L2 prefetch distance in tiles: half of the blocks of a kernel resident on

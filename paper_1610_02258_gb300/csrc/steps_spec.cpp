@@ -99,6 +99,7 @@ std::string policy_source(const HostModel &hm, int block) {
     std::ostringstream o;
     o << "namespace steps {\nnamespace {\nstruct SpecModel {\n";
     o << "    static constexpr bool kGlobalTrial = " << (spec_global_trial(hm) ? "true" : "false") << ";\n";
+    o << "    static constexpr bool kExpLeave = " << (hm.leave_exp ? "true" : "false") << ";\n";
     o << "    __device__ static int S(const ModelDev &) { return " << m.S << "; }\n";
     o << "    __device__ static int R(const ModelDev &) { return " << m.R << "; }\n";
     o << "    __device__ static uint32_t diffusive(const ModelDev &) { return " << hex_u32(m.diffusive) << "; }\n";

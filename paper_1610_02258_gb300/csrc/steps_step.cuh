@@ -179,6 +179,7 @@ __device__ __forceinline__ float propensity(const float4 q, const int32_t *cnt, 
 template <bool Z>
 struct RtModel {
     static constexpr bool kGlobalTrial = false;  // trial counts in shared memory
+    static constexpr bool kExpLeave = false;     // the EULER leave law (species scale in shared memory)
     __device__ static int S(const ModelDev &m) { return m.S; }
     __device__ static int R(const ModelDev &m) { return m.R; }
     __device__ static uint32_t diffusive(const ModelDev &m) { return m.diffusive; }
@@ -350,6 +351,15 @@ __device__ __forceinline__ int32_t trial_count(const StepArgs &a, int s, int32_t
     return mm > N ? N : (int32_t)mm;
 }
 
+// The species factor of tet i's thresholds: the window's species scale R_s
+// (EULER), or the tet's own leave value L_{s,i} from the EXP table (the
+// tet's factor A is then its cumulative face shares).
+template <class P>
+__device__ __forceinline__ uint32_t species_R(const StepArgs &a, const uint32_t *s_scale, int s, int64_t i) {
+    if constexpr (P::kExpLeave) return __ldg(a.leave + (size_t)s * (size_t)a.Tpad + (size_t)i);
+    else return s_scale[s];
+}
+
 // Leave thresholds of one species: T_f = (A_f R_s) >> 31 (2^31 fixed point).
 __device__ __forceinline__ void species_thresholds(const uint4 &A, uint32_t R, uint32_t &T0, uint32_t &T1,
                                                    uint32_t &T2, uint32_t &T3) {
@@ -451,12 +461,12 @@ struct WarpWork {
 // trial molecule w (species in order): face f when T_{f-1} <= x < T_f with
 // x = w >> 1 and cumulative thresholds T, stay when x >= T_3. A mover is
 // added to the neighbour's entry of nxt and removed from the tet's count.
-template <int BLOCK>
+template <int BLOCK, class P>
 __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork &ww, uint32_t item,
                                               const int32_t *trial_all, size_t tstride, int32_t *cnt_all,
                                               const uint4 *s_thr,
                                               const int4 *s_nbr, const uint32_t *s_tet, const uint32_t *s_scale,
-                                              uint32_t c0, uint32_t c3) {
+                                              uint32_t c0, uint32_t c3, int64_t i0) {
     int lane, s;
     uint32_t k, before;
     if (item < (uint32_t)kMapCap) {
@@ -497,7 +507,7 @@ __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork 
     const size_t Tpad = (size_t)a.Tpad;
     const uint4 rw = philox4x32_10(a.key0, a.key1, c0, s_tet[t], k, (kPurposeDiff << 28) | c3);
     uint32_t T0, T1, T2, T3;
-    species_thresholds(A, s_scale[s], T0, T1, T2, T3);
+    species_thresholds(A, species_R<P>(a, s_scale, s, i0 + t), T0, T1, T2, T3);
     uint32_t w = 4u * k;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -506,7 +516,7 @@ __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork 
                 s = __ffs(hm) - 1;
                 hm &= hm - 1;
                 end += (uint32_t)trial_all[s * tstride + t];
-                species_thresholds(A, s_scale[s], T0, T1, T2, T3);
+                species_thresholds(A, species_R<P>(a, s_scale, s, i0 + t), T0, T1, T2, T3);
             }
             const uint32_t x = word_of(rw, q) >> 1;
             if (x < T3) {
@@ -796,7 +806,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
                     const int s = __ffs(walk) - 1;
                     walk &= walk - 1;
                     const int32_t M = cnt_all[s * BLOCK + t];
-                    if (M > 0 && (uint32_t)(((uint64_t)Aw * s_scale[s]) >> 31) != 0u) {
+                    if (M > 0 && (uint32_t)(((uint64_t)Aw * species_R<P>(a, s_scale, s, i0 + t)) >> 31) != 0u) {
                         trial_all[s * tstride + t] = M;
                         if (M >= kBulkMin) {
                             bm |= 1u << s;
@@ -812,7 +822,8 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
                 while (walk) {
                     const int s = __ffs(walk) - 1;
                     walk &= walk - 1;
-                    if ((uint32_t)(((uint64_t)Aw * s_scale[s]) >> 31) == 0u) continue;  // draws nothing
+                    if ((uint32_t)(((uint64_t)Aw * species_R<P>(a, s_scale, s, i0 + t)) >> 31) == 0u)
+                        continue;  // draws nothing
                     const int32_t M = trial_count(a, s, cnt_all[s * BLOCK + t], (touched >> s) & 1u, O, tS,
                                                   s_tet[t], c0, c3, rblk, rb);
                     if (M > 0) {
@@ -833,8 +844,8 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         while (bm) {
             const int s = __ffs(bm) - 1;
             bm &= bm - 1;
-            cnt_all[s * BLOCK + t] -= bulk_species(a, s, trial_all[s * tstride + t], s_thr[t], s_scale[s], s_nbr[t],
-                                                   s_tet[t], c0, c3);
+            cnt_all[s * BLOCK + t] -= bulk_species(a, s, trial_all[s * tstride + t], s_thr[t],
+                                                   species_R<P>(a, s_scale, s, i0 + t), s_nbr[t], s_tet[t], c0, c3);
         }
         // the chunk's Philox blocks: exclusive prefix of the lanes' block counts
         const uint32_t nb = (W + 3u) >> 2;
@@ -869,7 +880,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         __syncwarp();
         if (ch < (uint32_t)rchunks) continue;  // diffusion in phase 2
         for (uint32_t item = lane; item < total; item += 32)
-            diffuse_block<BLOCK>(a, ww, item, trial_all, tstride, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3);
+            diffuse_block<BLOCK, P>(a, ww, item, trial_all, tstride, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3, i0);
         __syncwarp();
         if (valid) apply_remaining<BLOCK, P>(m, a, cnt_all, t, s_nz[t] | touched, i0);
         __syncwarp();
@@ -883,7 +894,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
             const WarpWork &ww = wwork[c];
             const uint32_t total = ww.first[32];
             for (uint32_t item = tid; item < total; item += BLOCK)
-                diffuse_block<BLOCK>(a, ww, item, trial_all, tstride, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3);
+                diffuse_block<BLOCK, P>(a, ww, item, trial_all, tstride, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3, i0);
         }
         __syncthreads();
         for (int c = tid >> 5; c < rchunks; c += BLOCK / 32) {
