@@ -17,6 +17,7 @@ of that size.
 """
 import copy
 import math
+import os
 
 import numpy as np
 import pytest
@@ -64,7 +65,7 @@ def _run_oracle(verts, tets, model, counts, masks, seed, t_end):
     o.set_counts(counts)
     for r, m in masks.items():
         o.set_reac_mask(r, m)
-    o.run(t_end)
+    o.run(t_end, threads=max(1, min(32, os.cpu_count() or 1)))  # the serial result, bit for bit
     return o.get_counts(), o.windows
 
 

@@ -8,6 +8,7 @@ runs are bit-exact against it; against the FP64 oracle the reaction phase is
 compared in distribution (two-sample KS p > 0.01, means within 3 standard
 errors over 10^4 replicates)."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -18,6 +19,9 @@ from oracle import END, OCC
 from paper_1610_02258_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
+
+# the oracle's threaded windows give its serial result bit for bit
+THREADS = max(1, min(32, os.cpu_count() or 1))
 
 
 @pytest.fixture(scope="module")
@@ -31,10 +35,11 @@ def capi():
     return c
 
 
-def run_both(capi, verts, tets, model, counts, seed, t_end, occ=OCC, masks=None, prec=32, **kw):
-    g = capi.Simulation(verts, tets, model, seed, occupancy=occ, **kw)
+def run_both(capi, verts, tets, model, counts, seed, t_end, occ=OCC, masks=None, prec=32, threads=1, leave=0,
+             **kw):
+    g = capi.Simulation(verts, tets, model, seed, occupancy=occ, leave_law=leave, **kw)
     g.set_counts(counts)
-    o = oracle.OracleSim(verts, tets, model, seed=seed, occ=occ, prec=prec)
+    o = oracle.OracleSim(verts, tets, model, seed=seed, occ=occ, prec=prec, leave=leave)
     o.set_counts(counts)
     for r, m in (masks or {}).items():
         g.set_reac_mask(r, m)
@@ -42,7 +47,7 @@ def run_both(capi, verts, tets, model, counts, seed, t_end, occ=OCC, masks=None,
     assert g.tau == o.tau
     for t in np.atleast_1d(t_end):
         g.run(t)
-        o.run(t)
+        o.run(t, threads=threads)
     assert g.windows == o.windows
     assert g.time == o.time
     return g.get_counts(), o.get_counts(), g, o
@@ -137,9 +142,29 @@ def test_full_size_config2_whole_run_bit_exact(capi):
     default launch configuration (Morton order, CUDA graph, 256 threads, the
     step kernel compiled for the model)."""
     w = I.config2()
-    gc, oc, g, o = run_both(capi, w.verts, w.tets, w.model, w.counts, w.seed, w.t_end)
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, w.model, w.counts, w.seed, w.t_end, threads=THREADS)
     assert g.specialized
     assert g.windows == 99
+    assert np.array_equal(gc, oc)
+
+
+def test_full_size_dense_box_whole_run_bit_exact(capi):
+    """The benchmark box at ten times its densities (294,780 tets, ~137
+    molecules per tet, 20M reaction events over the run), 20 ms: most
+    draws take the bit-plane path, the rest one word per molecule."""
+    w = I.config2(density_scale=10.0)
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, w.model, w.counts, w.seed, w.t_end, threads=THREADS)
+    assert g.windows == 99 and o.events > 10_000_000
+    assert np.array_equal(gc, oc)
+
+
+@pytest.mark.parametrize("mode", ["exp", "end"])
+def test_full_size_box_other_modes_bit_exact(capi, mode):
+    """The benchmark box at full size under the EXP leave law, and in the
+    end-count trial mode, ending off the window grid."""
+    w = I.config2()
+    kw = {"leave": oracle.EXP} if mode == "exp" else {"occ": END}
+    gc, oc, g, o = run_both(capi, w.verts, w.tets, w.model, w.counts, w.seed, [7.3e-3, w.t_end], threads=THREADS, **kw)
     assert np.array_equal(gc, oc)
 
 
