@@ -226,6 +226,19 @@ def cpu_baseline(w, windows_all: int, windows_one: int):
                             "sample": f"{windows_one} full windows ({dt_one:.1f} s), serial C, FP64"}}
 
 
+def cpu_baseline_dendrite(I, windows_all: int, windows_one: int):
+    """The oracle on the dendrite (1.03M tets, 20 species, masked influx), a
+    reduced run from its initial counts, on every host core and on one."""
+    w = I.config3()
+    cores = host_cores()
+    rate_all, dt_all = oracle_rate(w, windows_all, threads=cores)
+    rate_one, dt_one = oracle_rate(w, windows_one, threads=1)
+    return {"value": rate_all, "unit": UNIT, "cores": cores, "workload": w.name,
+            "sample": f"{windows_all} full windows ({dt_all:.1f} s) on {cores} threads, FP64",
+            "single_core": {"value": rate_one, "unit": UNIT, "cores": 1,
+                            "sample": f"{windows_one} full windows ({dt_one:.1f} s), serial C, FP64"}}
+
+
 def roofline(S: int, masked: bool, tets: int, kernel_s: float, peak: float, peak_kind: str, tr, sm_mhz,
              issue_bound: bool):
     """Roofline object of a plain step launch. hbm: algorithmic bytes per
@@ -686,6 +699,8 @@ def run_ours(args):
                          "served": measure_served(args, capi, I) if args.served_jobs > 0 else None}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, 4 * args.cpu_windows, max(5, args.cpu_windows // 4))
+        if args.dendrite_ms > 0 and args.workload == "irregular-box":
+            line["cpu_baseline"]["dendrite"] = cpu_baseline_dendrite(I, 20, 5)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
