@@ -108,8 +108,9 @@ int group_of(steps_server *srv, const steps_sim *proto, int *out) {
         g.own_stream = true;
     }
     try {
-        srv->groups.push_back(std::move(g));
+        srv->groups.push_back(g);
     } catch (const std::bad_alloc &) {
+        if (g.own_stream) cudaStreamDestroy(g.stream);
         steps::set_error("steps_server_submit: out of host memory");
         return STEPS_ERR_OOM;
     }
@@ -233,14 +234,17 @@ int steps_server_submit(steps_server *srv, const steps_sim *proto, uint64_t seed
     j.seed = seed;
     j.t_end = t_end;
     try {
+        // everything that can fail first; then the job is stored without reallocation
         j.counts.assign(counts, counts + (size_t)ns * (size_t)nt);
-        srv->jobs.push_back(std::move(j));
-        srv->job_group.push_back(grp);
-        srv->queue.push_back((int64_t)srv->jobs.size() - 1);
+        srv->jobs.reserve(srv->jobs.size() + 1);
+        srv->job_group.reserve(srv->job_group.size() + 1);
+        srv->queue.push_back((int64_t)srv->jobs.size());
     } catch (const std::bad_alloc &) {
         steps::set_error("steps_server_submit: out of host memory");
         return STEPS_ERR_OOM;
     }
+    srv->jobs.push_back(std::move(j));
+    srv->job_group.push_back(grp);
     *job = (int64_t)srv->jobs.size() - 1;
     return STEPS_OK;
 }
