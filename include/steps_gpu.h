@@ -371,8 +371,9 @@ int steps_server_stats(const steps_server *srv, uint64_t *rounds, uint64_t *rebu
  * make that first call before any stream capture. Synchronises with the
  * simulation's stream before returning.
  * Errors: d_counts holding a negative count gives STEPS_ERR_ARG before
- * anything changes (clock and d_counts as before the call); otherwise as
- * steps_run.
+ * anything changes (clock and d_counts as before the call); so does a
+ * simulation under STEPS_LEAVE_EXP (a shortened window would need a table
+ * built on the host); otherwise as steps_run.
  */
 int steps_run_noalloc(steps_sim *sim, int32_t *d_counts, double t_end);
 
