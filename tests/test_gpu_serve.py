@@ -90,3 +90,26 @@ def test_native_server_jobs_equal_alone_and_budget_admission(serve):
         st = srv.stats()
         assert st["running"] == 0 and st["queued"] == 0 and st["device_bytes"] == 0
         srv.close()
+
+
+def test_native_server_separates_leave_laws(serve):
+    """Prototypes of one model under the EULER and the EXP leave law are two
+    model structures for the server: their jobs run in two groups, each on
+    its own specialised kernel, and every job equals its run alone."""
+    from paper_1610_02258_gb300 import capi
+    w = I.config2(seed=9, nx=3, t_end=2e-3)
+    protos = [capi.from_workload(w, specialize=1), capi.from_workload(w, leave_law=capi.STEPS_LEAVE_EXP)]
+    specs = [(0, 21, 1.3e-3), (1, 22, 1.3e-3), (1, 23, 2.0e-3), (0, 24, 0.7e-3)]
+    srv = capi.NativeServer(max_jobs=4, wave_windows=3, specialize=1)
+    ids = [srv.submit(protos[k], seed, w.counts, t) for k, seed, t in specs]
+    for _ in range(1000):
+        srv.step()
+        if all(srv.state(i)[0] == 2 for i in ids):
+            break
+    for i, (k, seed, t) in zip(ids, specs):
+        got = srv.take_result(i)
+        ref = protos[k].clone(seed)
+        ref.set_counts(w.counts)
+        ref.run(t)
+        assert np.array_equal(got, ref.get_counts()), (k, seed)
+    srv.close()
