@@ -453,9 +453,11 @@ struct WarpWork {
     uint32_t W[32];           // trial molecules (words) of the tet
     uint32_t touched[32];     // species its reactions changed
     uint32_t first[33];       // exclusive prefix of the lanes' block counts
-    uint32_t map_own[kMapCap];  // lane | species << 5 | block-in-tet << 10
-    uint32_t map_before[kMapCap];
+    uint32_t map[kMapCap];    // lane | species << 5 | block-in-tet << 10 | words before the species << 17
 };
+// A tet's word stream holds fewer than kBulkMin trial molecules of each
+// species, so a block index fits the map's 7 bits and a word offset its 15.
+static_assert((kBulkMin - 1) * kMaxSpecies <= 4 * 128, "block-in-tet field of the map");
 
 // One Philox block (4 words) of a tet's diffusion stream: word w decides
 // trial molecule w (species in order): face f when T_{f-1} <= x < T_f with
@@ -470,11 +472,11 @@ __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork 
     int lane, s;
     uint32_t k, before;
     if (item < (uint32_t)kMapCap) {
-        const uint32_t o = ww.map_own[item];
+        const uint32_t o = ww.map[item];
         lane = (int)(o & 31u);
         s = (int)((o >> 5) & 31u);
-        k = o >> 10;
-        before = ww.map_before[item];
+        k = (o >> 10) & 127u;
+        before = o >> 17;
     } else {
         // the owner: last lane with first[lane] <= item; the species: walk the tet's
         // species until the block's first word
@@ -800,52 +802,42 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         if (valid) {
             uint32_t walk = (s_nz[t] | touched) & P::diffusive(m);
             const uint32_t Aw = s_thr[t].w;
-            if (!touched || !a.occ) {
-                // no occupancy rounding: the trial count is the count
-                while (walk) {
-                    const int s = __ffs(walk) - 1;
-                    walk &= walk - 1;
-                    const int32_t M = cnt_all[s * BLOCK + t];
-                    if (M > 0 && (uint32_t)(((uint64_t)Aw * species_R<P>(a, s_scale, s, i0 + t)) >> 31) != 0u) {
-                        trial_all[s * tstride + t] = M;
-                        if (M >= kBulkMin) {
-                            bm |= 1u << s;
-                        } else {
-                            hm |= 1u << s;
-                            W += (uint32_t)M;
-                        }
-                    }
-                }
-            } else {
-                uint32_t rblk = 0xFFFFFFFFu;
-                uint4 rb = make_uint4(0, 0, 0, 0);
-                while (walk) {
-                    const int s = __ffs(walk) - 1;
-                    walk &= walk - 1;
-                    if ((uint32_t)(((uint64_t)Aw * species_R<P>(a, s_scale, s, i0 + t)) >> 31) == 0u)
-                        continue;  // draws nothing
-                    const int32_t M = trial_count(a, s, cnt_all[s * BLOCK + t], (touched >> s) & 1u, O, tS,
-                                                  s_tet[t], c0, c3, rblk, rb);
-                    if (M > 0) {
-                        trial_all[s * tstride + t] = M;
-                        if (M >= kBulkMin) {
-                            bm |= 1u << s;
-                        } else {
-                            hm |= 1u << s;
-                            W += (uint32_t)M;
-                        }
+            // one loop for lanes with and without occupancy rounding (a reacting
+            // chunk holds both); without it the trial count is the count
+            const bool plain = !touched || !a.occ;
+            uint32_t rblk = 0xFFFFFFFFu;
+            uint4 rb = make_uint4(0, 0, 0, 0);
+            while (walk) {
+                const int s = __ffs(walk) - 1;
+                walk &= walk - 1;
+                if ((uint32_t)(((uint64_t)Aw * species_R<P>(a, s_scale, s, i0 + t)) >> 31) == 0u)
+                    continue;  // draws nothing
+                const int32_t N = cnt_all[s * BLOCK + t];
+                const int32_t M = plain ? N
+                                        : trial_count(a, s, N, (touched >> s) & 1u, O, tS, s_tet[t], c0, c3, rblk, rb);
+                if (M > 0) {
+                    trial_all[s * tstride + t] = M;
+                    if (M >= kBulkMin) {
+                        bm |= 1u << s;
+                    } else {
+                        hm |= 1u << s;
+                        W += (uint32_t)M;
                     }
                 }
             }
         }
         // species with many trial molecules: bit-plane draws by the lane that
         // owns the tet, movers sent now (they are rare unless counts are high,
-        // and then every lane has some)
-        while (bm) {
-            const int s = __ffs(bm) - 1;
-            bm &= bm - 1;
-            cnt_all[s * BLOCK + t] -= bulk_species(a, s, trial_all[s * tstride + t], s_thr[t],
-                                                   species_R<P>(a, s_scale, s, i0 + t), s_nbr[t], s_tet[t], c0, c3);
+        // and then every lane has some). The warp walks the union of its lanes'
+        // bulk species in species order, so that the lanes drawing for one
+        // species (similar counts, the same thresholds' scale) run together.
+        uint32_t bw = __reduce_or_sync(0xFFFFFFFFu, bm);
+        while (bw) {
+            const int s = __ffs(bw) - 1;
+            bw &= bw - 1;
+            if ((bm >> s) & 1u)
+                cnt_all[s * BLOCK + t] -= bulk_species(a, s, trial_all[s * tstride + t], s_thr[t],
+                                                       species_R<P>(a, s_scale, s, i0 + t), s_nbr[t], s_tet[t], c0, c3);
         }
         // the chunk's Philox blocks: exclusive prefix of the lanes' block counts
         const uint32_t nb = (W + 3u) >> 2;
@@ -873,8 +865,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
                     before = end;
                     end += (uint32_t)trial_all[s * tstride + t];
                 }
-                ww.map_own[first + k] = (uint32_t)lane | ((uint32_t)s << 5) | (k << 10);
-                ww.map_before[first + k] = before;
+                ww.map[first + k] = (uint32_t)lane | ((uint32_t)s << 5) | (k << 10) | (before << 17);
             }
         }
         __syncwarp();
