@@ -74,7 +74,14 @@ typedef struct steps_options {
                             least 65,536 tets and NVRTC is available (default), 1 = always (sim creation fails
                             with STEPS_ERR_CUDA if it cannot be built), -1 = never (the generic kernel) */
     int32_t leave_law;   /* STEPS_LEAVE_EULER (default) or STEPS_LEAVE_EXP */
-    int32_t reserved[2]; /* set to 0 */
+    int32_t flow;        /* launch form of a run's consecutive full windows on the model-specialised kernel.
+                            Flow: one launch for all of them, in which each tile of a window starts as soon as
+                            the tiles holding its face neighbours have finished the previous window. Window
+                            launches: one launch per window (graph replay as use_graph says). 0 (default): the
+                            first run with at least 48 full windows times both on its own windows and keeps the
+                            faster (steps_sim_flow reports it); 1: flow; -1: window launches. The results are
+                            the same bits in every form. */
+    int32_t reserved[1]; /* set to 0 */
 } steps_options;
 
 /* Fill *opt with the defaults. */
@@ -206,6 +213,11 @@ int steps_run_record(steps_sim *sim, double t_end, double dt_rec, int32_t n_spec
  * model (see steps_options.specialize), else 0. The two kernels give the same
  * results bit for bit; the specialised one takes fewer instructions. */
 int steps_sim_specialized(const steps_sim *sim, int32_t *specialized);
+
+/* *active = 1 when the simulation's full windows run as flow launches (steps_options.flow), else 0.
+ * tune_ms (may be NULL): [2] ms per window of window launches and of flow launches measured by the
+ * tuning run (0 before it, or without one). */
+int steps_sim_flow(const steps_sim *sim, int32_t *active, float *tune_ms);
 
 /* Tets and species of a simulation (either output may be NULL). */
 int steps_sim_shape(const steps_sim *sim, int64_t *nt, int32_t *n_species);
@@ -396,6 +408,12 @@ int steps_debug_logf(const float *x, int64_t n, float *out);
  * ends, so the device stays usable. limit_cycles: 1 .. 2^31 (about a second
  * at most); else STEPS_ERR_ARG. */
 int steps_debug_wait(int32_t deliver, int64_t limit_cycles);
+/* The flow launch's bounded wait for the tiles a tile depends on, on its own
+ * (a test of the failure path). One warp waits for 40 listed tiles to have
+ * finished window 4: with deliver != 0 they all have (STEPS_OK); with
+ * deliver = 0 one has not, and the wait gives up after limit_cycles clock
+ * cycles (STEPS_ERR_TIMEOUT). limit_cycles: 1 .. 2^31; else STEPS_ERR_ARG. */
+int steps_debug_flow_wait(int32_t deliver, int64_t limit_cycles);
 /* The host-side set-up of steps_sim_create alone, with no device work (for
  * tests of the host logic without a GPU): *tau (§2.1), the cumulative face
  * thresholds of every tet at the full window ([nt*4] uint32, 2^31 fixed

@@ -32,10 +32,10 @@ EXPORTS = [
     "steps_last_error", "steps_debug_philox", "steps_debug_logf", "steps_run_noalloc",
     "steps_batch_options_default", "steps_batch_create", "steps_batch_destroy", "steps_batch_run",
     "steps_batch_info", "steps_sim_clone", "steps_sim_device_bytes", "steps_set_reac_rate", "steps_run_record",
-    "steps_sim_specialized", "steps_batch_specialized", "steps_sim_shape",
+    "steps_sim_specialized", "steps_sim_flow", "steps_batch_specialized", "steps_sim_shape",
     "steps_server_options_default", "steps_server_create", "steps_server_destroy", "steps_server_submit",
     "steps_server_step", "steps_server_job_state", "steps_server_take_result", "steps_server_stats",
-    "steps_debug_host_tables", "steps_debug_wait",
+    "steps_debug_host_tables", "steps_debug_wait", "steps_debug_flow_wait",
 ]
 
 
@@ -48,7 +48,7 @@ class StepsError(RuntimeError):
 class steps_options(ctypes.Structure):
     _fields_ = [("occupancy", ctypes.c_int32), ("reorder", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("specialize", ctypes.c_int32), ("leave_law", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("flow", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class steps_batch_options(ctypes.Structure):
@@ -89,6 +89,7 @@ def _load():
         "steps_debug_philox": (ctypes.c_int, [u64, P, i64, P]),
         "steps_debug_logf": (ctypes.c_int, [P, i64, P]),
         "steps_debug_wait": (ctypes.c_int, [ctypes.c_int32, i64]),
+        "steps_debug_flow_wait": (ctypes.c_int, [ctypes.c_int32, i64]),
         "steps_run_noalloc": (ctypes.c_int, [P, P, ctypes.c_double]),
         "steps_batch_options_default": (None, [ctypes.POINTER(steps_batch_options)]),
         "steps_batch_create": (ctypes.c_int, [P, i32, ctypes.POINTER(steps_batch_options), P, PP]),
@@ -100,6 +101,7 @@ def _load():
         "steps_sim_device_bytes": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64)]),
         "steps_set_reac_rate": (ctypes.c_int, [P, i32, ctypes.c_double]),
         "steps_sim_specialized": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
+        "steps_sim_flow": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
         "steps_batch_specialized": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32)]),
         "steps_sim_shape": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
         "steps_debug_host_tables": (ctypes.c_int, [P, P, i32, ctypes.POINTER(ctypes.c_double), P, P]),
@@ -264,6 +266,14 @@ def steps_sim_specialized(sim):
     return bool(v.value)
 
 
+def steps_sim_flow(sim):
+    """(active, [ms per window of window launches, of flow launches] from the tuning run)."""
+    v = ctypes.c_int32(0)
+    ms = (ctypes.c_float * 2)()
+    _check(lib.steps_sim_flow(sim, ctypes.byref(v), ms))
+    return bool(v.value), [float(ms[0]), float(ms[1])]
+
+
 def steps_get_time(sim):
     t = ctypes.c_double()
     _check(lib.steps_get_time(sim, ctypes.byref(t)))
@@ -309,6 +319,12 @@ def steps_debug_wait(deliver, limit_cycles):
     """The step kernel's bounded bulk-copy wait on its own: raises StepsError
     (code -6, STEPS_ERR_TIMEOUT) when the wait ran out."""
     _check(lib.steps_debug_wait(1 if deliver else 0, int(limit_cycles)))
+
+
+def steps_debug_flow_wait(deliver, limit_cycles):
+    """The flow launch's bounded wait for the tiles a tile depends on, on its
+    own: raises StepsError (code -6, STEPS_ERR_TIMEOUT) when the wait ran out."""
+    _check(lib.steps_debug_flow_wait(1 if deliver else 0, int(limit_cycles)))
 
 
 def steps_batch_options_default():
@@ -444,7 +460,7 @@ class Simulation:
     the calls above; counts are [S, nt] numpy arrays in the caller's tet order)."""
 
     def __init__(self, verts, tets, model, seed, occupancy=STEPS_OCC_MEAN, reorder=STEPS_REORDER_MORTON,
-                 block=256, use_graph=True, cuda_stream=None, specialize=0, leave_law=0):
+                 block=256, use_graph=True, cuda_stream=None, specialize=0, leave_law=0, flow=None):
         self.S = model.n_species
         self.R = model.n_reac
         self.nt = int(np.asarray(tets).shape[0])
@@ -457,6 +473,7 @@ class Simulation:
         opt.use_graph = 1 if use_graph else 0
         opt.specialize = int(specialize)
         opt.leave_law = int(leave_law)
+        opt.flow = 0 if flow is None else (1 if flow else -1)  # None: tuned
         self._sim = steps_sim_create(self._mesh, self._model, seed, opt, cuda_stream)
 
     def clone(self, seed, cuda_stream=None):
@@ -516,6 +533,11 @@ class Simulation:
     @property
     def specialized(self):
         return steps_sim_specialized(self._sim)
+
+    @property
+    def flow(self):
+        """(full windows run as flow launches, tuning ms per window [window launches, flow launches])."""
+        return steps_sim_flow(self._sim)
 
     @property
     def windows(self):

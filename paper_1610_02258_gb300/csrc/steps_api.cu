@@ -34,6 +34,7 @@ struct steps_model {
 namespace {
 
 constexpr int kGraphWindows = 16;  // full windows per captured graph (even: buffer parity is restored)
+constexpr int64_t kFlowTuneWindows = 48;  // windows the launch-form tuning takes (3 rounds of 2 groups)
 
 __global__ void scatter_to_device_order(const int32_t *src, int64_t nt, int32_t S, const int32_t *inv_perm,
                                         int32_t *dst, size_t Tpad) {
@@ -107,6 +108,16 @@ struct steps_sim {
     uint32_t scale_full[kMaxSpecies] = {};
     // graphs of kGraphWindows full windows, one per starting buffer
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // flow launches (a run's full windows in one persistent launch): each tile's
+    // neighbour tiles (tiles of opt.block tets in device order, CSR), the tiles'
+    // finished-window words and the item counter (d_flow[ntiles])
+    int32_t *d_tnb_off = nullptr;
+    int32_t *d_tnb = nullptr;
+    uint32_t *d_flow = nullptr;
+    int64_t ntiles = 0;
+    size_t flow_bytes = 0;
+    int flow_pick = -1;          // flow = 0 (auto): -1 not yet timed, 0 window launches, 1 flow launches
+    float flow_ms[2] = {0.f, 0.f};  // tuning: ms per window of window launches and of flow launches
 
     double time() const { return k_grid == 0 ? t_base : t_base + (double)k_grid * tab.tau; }
 
@@ -128,6 +139,54 @@ struct steps_sim {
         cudaFree(d_trial);
         cudaFree(d_leave[0]);
         cudaFree(d_leave[1]);
+        cudaFree(d_tnb_off);
+        cudaFree(d_tnb);
+        cudaFree(d_flow);
+    }
+
+    // the flow kernel's tables (once): tile t lists itself and every tile
+    // holding a face neighbour of one of its tets
+    int ensure_flow() {
+        if (d_flow) return STEPS_OK;
+        const int64_t B = opt.block;
+        const int64_t nt = (T + B - 1) / B;
+        std::vector<int32_t> off, nb, tmp;
+        try {
+            off.resize((size_t)nt + 1);
+            for (int64_t t = 0; t < nt; ++t) {
+                tmp.assign(1, (int32_t)t);
+                for (int64_t d = t * B; d < std::min(T, (t + 1) * B); ++d)
+                    for (int f = 0; f < 4; ++f) {
+                        const int32_t j = tab.nbr_dev[(size_t)(4 * d + f)];
+                        if (j >= 0 && j / B != t) tmp.push_back((int32_t)(j / B));
+                    }
+                std::sort(tmp.begin(), tmp.end());
+                tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+                off[(size_t)t] = (int32_t)nb.size();
+                nb.insert(nb.end(), tmp.begin(), tmp.end());
+            }
+            off[(size_t)nt] = (int32_t)nb.size();
+        } catch (const std::bad_alloc &) {
+            set_error("flow tables: out of host memory");
+            return STEPS_ERR_OOM;
+        }
+        if (!cuda_ok(cudaMalloc((void **)&d_tnb_off, off.size() * 4), "flow tables") ||
+            !cuda_ok(cudaMalloc((void **)&d_tnb, nb.size() * 4), "flow tables") ||
+            !cuda_ok(cudaMalloc((void **)&d_flow, ((size_t)nt + 1) * 4), "flow tables")) {
+            cudaFree(d_tnb_off);
+            cudaFree(d_tnb);
+            cudaFree(d_flow);
+            d_tnb_off = d_tnb = nullptr;
+            d_flow = nullptr;
+            return STEPS_ERR_OOM;
+        }
+        if (!cuda_ok(cudaMemcpy(d_tnb_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice), "flow tables") ||
+            !cuda_ok(cudaMemcpy(d_tnb, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice), "flow tables") ||
+            !cuda_ok(cudaMemset(d_flow, 0, ((size_t)nt + 1) * 4), "flow tables"))
+            return STEPS_ERR_CUDA;
+        ntiles = nt;
+        flow_bytes = (off.size() + nb.size() + (size_t)nt + 1) * 4;
+        return STEPS_OK;
     }
 
     // EXP leave law: the table of a window of length tau_k, into the full
@@ -239,7 +298,62 @@ struct steps_sim {
         return rc;
     }
 
+    // n full windows: flow launches or window launches (both give the same bits)
     int full_windows(int64_t n) {
+        if (spec && opt.flow == 0 && flow_pick < 0 && n >= kFlowTuneWindows) {
+            int64_t used = 0;
+            int rc = tune_flow(&used);
+            if (rc) return rc;
+            n -= used;
+        }
+        if (spec && n >= 2 && (opt.flow == 1 || (opt.flow == 0 && flow_pick == 1))) return flow_windows(n);
+        return window_launches(n);
+    }
+
+    // The first run with enough full windows times both launch forms on
+    // alternating groups of windows (after one warm group of each, so that
+    // one-time costs and the state's slow drift do not decide) and keeps the
+    // flow launches when they are more than 2 % faster. The windows taken
+    // are ordinary windows of the run.
+    int tune_flow(int64_t *used) {
+        int rc = ensure_flow();
+        if (rc) return rc;
+        cudaEvent_t e[4] = {};
+        for (auto &ev : e)
+            if (!cuda_ok(cudaEventCreate(&ev), "flow tuning event")) {
+                for (auto &x : e)
+                    if (x) cudaEventDestroy(x);
+                return STEPS_ERR_CUDA;
+            }
+        float tot[2] = {0.f, 0.f};
+        const int64_t g = kFlowTuneWindows / 6;  // windows per group: warm, then two timed rounds
+        for (int round = 0; round < 3 && rc == STEPS_OK; ++round) {
+            if (!cuda_ok(cudaEventRecord(e[0], stream), "flow tuning")) rc = STEPS_ERR_CUDA;
+            if (!rc) rc = window_launches(g);
+            if (!rc && !cuda_ok(cudaEventRecord(e[1], stream), "flow tuning")) rc = STEPS_ERR_CUDA;
+            if (!rc) rc = flow_windows(g);
+            if (!rc && !cuda_ok(cudaEventRecord(e[2], stream), "flow tuning")) rc = STEPS_ERR_CUDA;
+            float a = 0.f, b = 0.f;
+            if (!rc && (!cuda_ok(cudaEventSynchronize(e[2]), "flow tuning") ||
+                        !cuda_ok(cudaEventElapsedTime(&a, e[0], e[1]), "flow tuning") ||
+                        !cuda_ok(cudaEventElapsedTime(&b, e[1], e[2]), "flow tuning")))
+                rc = STEPS_ERR_CUDA;
+            if (!rc && round > 0) {
+                tot[0] += a;
+                tot[1] += b;
+            }
+            *used += 2 * g;
+        }
+        for (auto &x : e) cudaEventDestroy(x);
+        if (rc) return rc;
+        flow_ms[0] = tot[0] / (2.f * (float)g);
+        flow_ms[1] = tot[1] / (2.f * (float)g);
+        flow_pick = tot[1] < 0.98f * tot[0] ? 1 : 0;
+        return STEPS_OK;
+    }
+
+    // n full windows, one launch each (graph replay of kGraphWindows at a time)
+    int window_launches(int64_t n) {
         int64_t done = 0;
         if (opt.use_graph && n >= kGraphWindows) {
             if (!graph[cur]) {
@@ -263,6 +377,33 @@ struct steps_sim {
             ++launches;
             cur = 1 - cur;
             ++k_total;
+        }
+        return STEPS_OK;
+    }
+
+    // n full windows through persistent launches of the flow kernel (one per
+    // 2^31 items)
+    int flow_windows(int64_t n) {
+        int rc = ensure_flow();
+        if (rc) return rc;
+        const int64_t cap = std::max<int64_t>(1, (int64_t)0x7FFFFFFF / ntiles);
+        for (int64_t done = 0; done < n;) {
+            const int64_t nw = std::min(n - done, cap);
+            if (!cuda_ok(cudaMemsetAsync(d_flow + ntiles, 0, 4, stream), "flow counter")) return STEPS_ERR_CUDA;
+            StepArgs a = args(cur, k_total, nullptr, tab.tau, scale_full);
+            FlowArgs f;
+            f.tnb_off = d_tnb_off;
+            f.tnb = d_tnb;
+            f.tile_done = d_flow;
+            f.fetch = d_flow + ntiles;
+            f.nwin = (uint32_t)nw;
+            f.ntiles = (uint32_t)ntiles;
+            rc = launch_spec_flow(spec, model.dev, a, f, opt.block, stream);
+            if (rc) return rc;
+            ++launches;
+            done += nw;
+            k_total += (uint64_t)nw;
+            if (nw & 1) cur = 1 - cur;
         }
         return STEPS_OK;
     }
@@ -360,6 +501,10 @@ int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t 
         }
         if (s->opt.leave_law != STEPS_LEAVE_EULER && s->opt.leave_law != STEPS_LEAVE_EXP) {
             set_error("steps_sim_create: bad leave law");
+            return STEPS_ERR_ARG;
+        }
+        if (s->opt.flow < -1 || s->opt.flow > 1) {
+            set_error("steps_sim_create: flow must be 0 (tuned), 1 (on) or -1 (off)");
             return STEPS_ERR_ARG;
         }
         if (s->opt.leave_law == STEPS_LEAVE_EXP) {
@@ -535,7 +680,7 @@ int steps_sim_device_bytes(const steps_sim *sim, int64_t *bytes) {
     const int64_t Tpad = sim->Tpad, S = sim->S, T = sim->T;
     *bytes = 2 * S * Tpad * 4 + Tpad * 16 * 2 + Tpad * 4 + 16 + S * T * 4 + (sim->d_orig ? Tpad * 4 + T * 4 : 0) +
              (sim->d_trial ? S * Tpad * 4 : 0) + (sim->d_leave[0] ? 2 * S * Tpad * 4 : 0) +
-             (sim->d_rmask ? Tpad * 4 : 0);
+             (sim->d_rmask ? Tpad * 4 : 0) + (int64_t)sim->flow_bytes;
     return STEPS_OK;
 }
 
@@ -709,6 +854,12 @@ int finish_run(steps_sim *sim, const char *who) {
                                          "a copy may still be in flight, so this simulation is closed to further runs");
             return STEPS_ERR_TIMEOUT;
         }
+        if (err & 8u) {
+            sim->failed = true;
+            set_error(std::string(who) + ": a tile of a flow launch waited beyond its limit for the tiles it depends "
+                                         "on; the counts are not valid, so this simulation is closed to further runs");
+            return STEPS_ERR_TIMEOUT;
+        }
         set_error(std::string(who) + (err & 2u ? ": a tet fired more than 2^24 reactions in one window (rates too large)"
                                                : ": a negative count was seen on the device"));
         return STEPS_ERR_STATE;
@@ -828,6 +979,17 @@ int steps_run_record(steps_sim *sim, double t_end, double dt_rec, int32_t n_spec
     return rc;
 }
 
+int steps_sim_flow(const steps_sim *sim, int32_t *active, float *tune_ms) {
+    CHECK_NULL(sim, "steps_sim_flow");
+    CHECK_NULL(active, "steps_sim_flow");
+    *active = sim->spec && (sim->opt.flow == 1 || (sim->opt.flow == 0 && sim->flow_pick == 1)) ? 1 : 0;
+    if (tune_ms) {
+        tune_ms[0] = sim->flow_ms[0];
+        tune_ms[1] = sim->flow_ms[1];
+    }
+    return STEPS_OK;
+}
+
 int steps_sim_specialized(const steps_sim *sim, int32_t *specialized) {
     CHECK_NULL(sim, "steps_sim_specialized");
     CHECK_NULL(specialized, "steps_sim_specialized");
@@ -932,6 +1094,54 @@ int steps_debug_wait(int32_t deliver, int64_t limit_cycles) {
     }
     if (st != 0u) {
         set_error("steps_debug_wait: unexpected status");
+        return STEPS_ERR_STATE;
+    }
+    return STEPS_OK;
+}
+
+int steps_debug_flow_wait(int32_t deliver, int64_t limit_cycles) {
+    if (limit_cycles < 1 || limit_cycles > (int64_t)1 << 31) {
+        set_error("steps_debug_flow_wait: limit_cycles must be in [1, 2^31]");
+        return STEPS_ERR_ARG;
+    }
+    // tile 0 lists 40 neighbour tiles (two rounds of the warp); all of them
+    // have finished window 4 (word 5) when delivered, else the last has not
+    constexpr int n = 40;
+    int32_t h_off[2] = {0, n}, h_nb[n];
+    uint32_t h_done[n];
+    for (int j = 0; j < n; ++j) {
+        h_nb[j] = j;
+        h_done[j] = 5u + (uint32_t)(j % 3);
+    }
+    if (!deliver) h_done[n - 1] = 4u;
+    int32_t *d_off = nullptr, *d_nb = nullptr;
+    uint32_t *d_done = nullptr, *status = nullptr;
+    int rc = STEPS_OK;
+    if (!cuda_ok(cudaMalloc((void **)&d_off, sizeof(h_off)), "steps_debug_flow_wait: alloc") ||
+        !cuda_ok(cudaMalloc((void **)&d_nb, sizeof(h_nb)), "steps_debug_flow_wait: alloc") ||
+        !cuda_ok(cudaMalloc((void **)&d_done, sizeof(h_done)), "steps_debug_flow_wait: alloc") ||
+        !cuda_ok(cudaMalloc((void **)&status, 4), "steps_debug_flow_wait: alloc"))
+        rc = STEPS_ERR_OOM;
+    uint32_t st = 0;
+    if (!rc && (!cuda_ok(cudaMemcpy(d_off, h_off, sizeof(h_off), cudaMemcpyHostToDevice), "steps_debug_flow_wait") ||
+                !cuda_ok(cudaMemcpy(d_nb, h_nb, sizeof(h_nb), cudaMemcpyHostToDevice), "steps_debug_flow_wait") ||
+                !cuda_ok(cudaMemcpy(d_done, h_done, sizeof(h_done), cudaMemcpyHostToDevice), "steps_debug_flow_wait") ||
+                !cuda_ok(cudaMemset(status, 0xFF, 4), "steps_debug_flow_wait")))
+        rc = STEPS_ERR_CUDA;
+    if (!rc) rc = launch_flow_wait_test(d_off, d_nb, d_done, (long long)limit_cycles, status);
+    if (!rc && !cuda_ok(cudaMemcpy(&st, status, 4, cudaMemcpyDeviceToHost), "steps_debug_flow_wait"))
+        rc = STEPS_ERR_CUDA;
+    cudaFree(d_off);
+    cudaFree(d_nb);
+    cudaFree(d_done);
+    cudaFree(status);
+    if (rc) return rc;
+    if (st == 8u) {
+        set_error("steps_debug_flow_wait: the dependency wait did not complete within its limit");
+        return STEPS_ERR_TIMEOUT;
+    }
+    if (st != 0u) {
+        set_error("steps_debug_flow_wait: unexpected status");
         return STEPS_ERR_STATE;
     }
     return STEPS_OK;

@@ -88,6 +88,18 @@ struct StepArgs {
     uint32_t scale[kMaxSpecies];  // per-species fixed-point scale for this window length
 };
 
+// Full windows of one simulation in one persistent launch (flow_tiles): the
+// items are (window q, tile t), q-major; the item (q, t) waits until every
+// tile sharing a face with t, t included, has finished window q - 1.
+struct FlowArgs {
+    const int32_t *tnb_off;  // [ntiles + 1] offsets into tnb of each tile's neighbour tiles
+    const int32_t *tnb;      // neighbour tiles (each tile lists itself)
+    uint32_t *tile_done;     // [ntiles] low word of (last window the tile finished + 1)
+    uint32_t *fetch;         // item counter, zero when the launch starts
+    uint32_t nwin;           // windows a.window, a.window + 1, ... (nwin * ntiles < 2^31)
+    uint32_t ntiles;
+};
+
 // One member of a batched launch, resident in device memory. The step kernel
 // reads its member's model and arguments from here (cur/nxt chosen by
 // `parity`); the advance kernel moves `args.window` and `parity` after every

@@ -65,6 +65,8 @@ int launch_step(const ModelDev &m, const StepArgs &a, int block, void *stream);
 int launch_philox_test(uint64_t seed, const uint32_t *d_ctr, int64_t n, uint32_t *d_out, void *stream);
 int launch_logf_test(const float *d_x, int64_t n, float *d_out, void *stream);
 int launch_wait_test(const void *d_src, int deliver, long long limit, uint32_t *d_status, void *stream);
+int launch_flow_wait_test(const int32_t *d_off, const int32_t *d_nb, uint32_t *d_done, long long limit,
+                          uint32_t *d_status);
 int launch_add_u64(uint64_t *p, uint64_t v, void *stream);
 int launch_step_batch(const BlockWork *work, int64_t nblocks, RepEntry *reps, int max_S, int max_R,
                       bool any_order0, int block, void *stream);
@@ -75,6 +77,9 @@ int launch_advance(RepEntry *reps, int32_t n, void *stream);
 // nullptr (with the reason in *why) when they cannot be built.
 void *spec_kernel(const HostModel &hm, int block, std::string *why);
 int launch_spec(void *spec, const ModelDev &m, const StepArgs &a, int block, void *stream);
+// Full windows a.window .. a.window + f.nwin - 1 in one persistent launch of
+// the flow kernel (one block per resident slot); f.fetch must be zero.
+int launch_spec_flow(void *spec, const ModelDev &m, const StepArgs &a, const FlowArgs &f, int block, void *stream);
 int launch_spec_batch(void *spec, const BlockWork *work, int64_t nblocks, RepEntry *reps, int S, int block,
                       void *stream);
 std::string spec_program_source(const HostModel &hm, int block);

@@ -42,6 +42,22 @@ __global__ void wait_test_kernel(const uint4 *src, int deliver, long long limit,
     *status = mbar_wait_bounded(&bar, 0, limit) ? 0u : 4u;
 }
 
+// The flow kernel's bounded dependency wait on its own: one warp waits for
+// the tiles listed for tile 0 to reach window word 5. status: 0 completed,
+// 8 timed out (the flow kernel's error bit).
+__global__ void flow_wait_test_kernel(const int32_t *tnb_off, const int32_t *tnb, uint32_t *tile_done,
+                                      long long limit, uint32_t *status) {
+    FlowArgs f;
+    f.tnb_off = tnb_off;
+    f.tnb = tnb;
+    f.tile_done = tile_done;
+    f.fetch = nullptr;
+    f.nwin = 1;
+    f.ntiles = 1;
+    const bool ok = flow_deps_wait(f, 0u, 5u, limit);
+    if (threadIdx.x == 0) *status = ok ? 0u : 8u;
+}
+
 __global__ void add_u64_kernel(uint64_t *p, uint64_t v) { *p += v; }
 
 template <int BLOCK, int RM, bool Z>
@@ -145,6 +161,12 @@ int launch_philox_test(uint64_t seed, const uint32_t *d_ctr, int64_t n, uint32_t
 
 int launch_wait_test(const void *d_src, int deliver, long long limit, uint32_t *d_status, void *stream) {
     wait_test_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((const uint4 *)d_src, deliver, limit, d_status);
+    return cudaGetLastError() == cudaSuccess ? STEPS_OK : STEPS_ERR_CUDA;
+}
+
+int launch_flow_wait_test(const int32_t *d_off, const int32_t *d_nb, uint32_t *d_done, long long limit,
+                          uint32_t *d_status) {
+    flow_wait_test_kernel<<<1, 32>>>(d_off, d_nb, d_done, limit, d_status);
     return cudaGetLastError() == cudaSuccess ? STEPS_OK : STEPS_ERR_CUDA;
 }
 

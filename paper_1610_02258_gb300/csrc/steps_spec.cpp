@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -151,6 +152,10 @@ std::string program_source(const HostModel &hm, int block) {
       << "steps_spec_step(const __grid_constant__ steps::ModelDev m, const __grid_constant__ steps::StepArgs a) {\n"
       << "    steps::step_tile<" << block << ", " << reaction_bucket(hm.dev.R) << ", steps::SpecModel>(m, a, "
       << "(int64_t)blockIdx.x);\n}\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << (five ? 5 : 2048 / block / 2) << ")\n"
+      << "steps_spec_flow(const __grid_constant__ steps::ModelDev m, const __grid_constant__ steps::StepArgs a, "
+      << "const __grid_constant__ steps::FlowArgs f) {\n"
+      << "    steps::flow_tiles<" << block << ", " << reaction_bucket(hm.dev.R) << ", steps::SpecModel>(m, a, f);\n}\n";
     o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << 2048 / block / 2 << ")\n"
       << "steps_spec_batch(const steps::BlockWork *__restrict__ work, const steps::RepEntry *__restrict__ reps, "
       << "int32_t prefetch) {\n"
@@ -163,7 +168,9 @@ struct Compiled {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;        // plain step kernel
     cudaKernel_t kern_batch = nullptr;  // batched step kernel
+    cudaKernel_t kern_flow = nullptr;   // persistent kernel of a simulation's full windows
     size_t smem_set = 0;                // dynamic shared memory the plain kernel was opted in to
+    size_t smem_set_flow = 0;           // the flow kernel
     size_t smem_set_batch = 0;          // and the batched one
     bool global_trial = false;          // trial counts in StepArgs::trial, not shared memory
 };
@@ -225,7 +232,8 @@ Compiled *compiled(const HostModel &hm, int block, std::string *why) {
     c->global_trial = spec_global_trial(hm);
     if (cudaLibraryLoadData(&c->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
         cudaLibraryGetKernel(&c->kern, c->lib, "steps_spec_step") != cudaSuccess ||
-        cudaLibraryGetKernel(&c->kern_batch, c->lib, "steps_spec_batch") != cudaSuccess) {
+        cudaLibraryGetKernel(&c->kern_batch, c->lib, "steps_spec_batch") != cudaSuccess ||
+        cudaLibraryGetKernel(&c->kern_flow, c->lib, "steps_spec_flow") != cudaSuccess) {
         cudaGetLastError();
         if (why) *why = "loading the compiled kernel failed";
         g_cache[src] = nullptr;
@@ -279,6 +287,35 @@ int launch_spec(void *spec, const ModelDev &m, const StepArgs &a, int block, voi
     cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
     if (e != cudaSuccess) {
         set_error(std::string("specialised step kernel launch: ") + cudaGetErrorString(e));
+        return STEPS_ERR_CUDA;
+    }
+    return STEPS_OK;
+}
+
+int launch_spec_flow(void *spec, const ModelDev &m, const StepArgs &a, const FlowArgs &f, int block, void *stream) {
+    if (a.T <= 0 || f.nwin == 0) return STEPS_OK;
+    Compiled *c = static_cast<Compiled *>(spec);
+    const void *fn = (const void *)c->kern_flow;
+    const size_t smem = ((size_t)m.S + 1 + (c->global_trial ? 0 : (size_t)m.S)) * (size_t)block * sizeof(int32_t);
+    if (!opt_in(fn, smem, &c->smem_set_flow)) return STEPS_ERR_CUDA;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1) {
+        set_error("flow kernel occupancy: " + std::string(cudaGetErrorString(cudaGetLastError())));
+        return STEPS_ERR_CUDA;
+    }
+    StepArgs b = a;
+    b.window_base = nullptr;
+    // the item taken about half a resident wave later: its tables into L2
+    if (b.prefetch) b.prefetch = std::max(1, per_sm * sms / 2);
+    ModelDev mm = m;
+    FlowArgs ff = f;
+    void *args[3] = {(void *)&mm, (void *)&b, (void *)&ff};
+    const unsigned grid = f.nwin * f.ntiles;  // one item per block
+    cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3((unsigned)block), args, smem, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("flow step kernel launch: ") + cudaGetErrorString(e));
         return STEPS_ERR_CUDA;
     }
     return STEPS_OK;

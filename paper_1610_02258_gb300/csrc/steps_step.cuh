@@ -391,8 +391,8 @@ __device__ __forceinline__ void plane_compare(uint32_t T, int sh, uint32_t R, ui
 // decided (a comparison still open after all 31 planes has x = T: not less).
 // The movers go to the neighbours' entries of nxt, one atomic add per face;
 // returns how many left.
-__device__ __forceinline__ int32_t bulk_species(const StepArgs &a, int s, int32_t M, const uint4 A, uint32_t Rs,
-                                             const int4 nb, uint32_t key_tet, uint32_t c0, uint32_t c3) {
+__device__ __forceinline__ int32_t bulk_species(const StepArgs &a, int32_t *nxt, int s, int32_t M, const uint4 A,
+                                             uint32_t Rs, const int4 nb, uint32_t key_tet, uint32_t c0, uint32_t c3) {
     uint32_t T0, T1, T2, T3;
     species_thresholds(A, Rs, T0, T1, T2, T3);
     const uint32_t c3b = (kPurposeBulk << 28) | ((uint32_t)s << 23) | (c3 & 0x007FFFFFu);
@@ -426,7 +426,7 @@ __device__ __forceinline__ int32_t bulk_species(const StepArgs &a, int s, int32_
         n2 += __popc(l2 & ~l1);
         n3 += __popc(l3 & ~l2);
     }
-    int32_t *row = a.nxt + (size_t)s * (size_t)a.Tpad;
+    int32_t *row = nxt + (size_t)s * (size_t)a.Tpad;
     if (n0) atomicAdd(row + nb.x, n0);
     if (n1) atomicAdd(row + nb.y, n1);
     if (n2) atomicAdd(row + nb.z, n2);
@@ -464,7 +464,7 @@ static_assert((kBulkMin - 1) * kMaxSpecies <= 4 * 128, "block-in-tet field of th
 // x = w >> 1 and cumulative thresholds T, stay when x >= T_3. A mover is
 // added to the neighbour's entry of nxt and removed from the tet's count.
 template <int BLOCK, class P>
-__device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork &ww, uint32_t item,
+__device__ __forceinline__ void diffuse_block(const StepArgs &a, int32_t *nxt, const WarpWork &ww, uint32_t item,
                                               const int32_t *trial_all, size_t tstride, int32_t *cnt_all,
                                               const uint4 *s_thr,
                                               const int4 *s_nbr, const uint32_t *s_tet, const uint32_t *s_scale,
@@ -523,7 +523,7 @@ __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork 
             const uint32_t x = word_of(rw, q) >> 1;
             if (x < T3) {
                 const int nbr = x < T0 ? nb.x : x < T1 ? nb.y : x < T2 ? nb.z : nb.w;
-                atomicAdd(a.nxt + s * Tpad + nbr, 1);
+                atomicAdd(nxt + s * Tpad + nbr, 1);
                 atomicSub(&cnt_all[s * BLOCK + t], 1);
             }
             ++w;
@@ -539,9 +539,9 @@ __device__ __forceinline__ void diffuse_block(const StepArgs &a, const WarpWork 
 // holds the species that can be non-zero (non-zero at the start or changed by
 // a reaction).
 template <int BLOCK, class P>
-__device__ __forceinline__ void apply_remaining(const ModelDev &m, const StepArgs &a, const int32_t *cnt_all, int t,
-                                                uint32_t may, int64_t i0) {
-    int32_t *out = a.nxt + i0 + t;
+__device__ __forceinline__ void apply_remaining(const ModelDev &m, const StepArgs &a, int32_t *nxt,
+                                                const int32_t *cnt_all, int t, uint32_t may, int64_t i0) {
+    int32_t *out = nxt + i0 + t;
     const size_t Tpad = (size_t)a.Tpad;
     while (may) {
         const int s = __ffs(may) - 1;
@@ -573,8 +573,52 @@ __device__ __forceinline__ void apply_remaining(const ModelDev &m, const StepArg
 //         over the whole block, after a barrier, for chunks with reacting
 //         tets; then each tet's remaining counts are added to its own entry
 //         of `nxt`. Z: the model has order-0 reactions.
-template <int BLOCK, int RM, class P>
-__device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, const int64_t tile) {
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Called by one whole warp: waits until every neighbour tile of tile t has
+// published tile_done >= need (acquire loads, one neighbour per lane), for at
+// most `limit` cycles (by default 2^31, about a second; false on timeout). A
+// finished tile is published by its thread 0 with a release store after the
+// block's barrier; lane 0 then orders the tile's bulk copies (async proxy)
+// after these loads.
+__device__ __forceinline__ bool flow_deps_wait(const FlowArgs &f, uint32_t t, uint32_t need,
+                                               long long limit = 2ll << 30) {
+    const int lane = threadIdx.x & 31;
+    const int b0 = f.tnb_off[t], b1 = f.tnb_off[t + 1];
+    const long long t0 = clock64();
+    bool ok = true;
+    for (int base = b0; base < b1 && ok; base += 32) {
+        const int j = base + lane;
+        const uint32_t *p = j < b1 ? f.tile_done + f.tnb[j] : nullptr;
+        for (;;) {
+            const bool done = !p || (int32_t)(ld_acquire_gpu(p) - need) >= 0;
+            if (__all_sync(0xFFFFFFFFu, done)) break;
+            if (__any_sync(0xFFFFFFFFu, clock64() - t0 > limit)) {
+                ok = false;
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+    return ok;
+}
+
+// FLOW: the block takes its item (window q, tile) from f's counter instead
+// (a launch of several windows, flow_tiles). Returns false when the tile's
+// copies or the tiles it depends on did not arrive within the wait limits.
+template <int BLOCK, int RM, class P, bool FLOW = false>
+__device__ __forceinline__ bool step_tile(const ModelDev &m, const StepArgs &a, int64_t tile,
+                                          const FlowArgs *f = nullptr) {
     extern __shared__ __align__(16) int32_t smem[];  // cnt [S + 1][BLOCK], trial [S][BLOCK]
     __shared__ __align__(16) uint4 s_thr[BLOCK];
     __shared__ __align__(16) int4 s_nbr[BLOCK];
@@ -591,10 +635,38 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     __shared__ RxnTab tb;
     __shared__ uint32_t s_scale[kMaxSpecies];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_item;
 
     const int S = P::S(m);
     const int tid = threadIdx.x;
     const int lane = tid & 31;
+
+    // Programmatic dependent launch: the next window's grid may start its
+    // blocks as soon as every block of this one has started; they run up to
+    // griddepcontrol.wait below (set-up and the copies of the constant tables)
+    // while this grid drains. Without such a launch both are no-ops.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
+    if (tid == 0) {
+        nreact = 0;
+        ncalm = 0;
+        next_chunk = 0;
+        mbar_init(&bar, 1);
+        if constexpr (FLOW) s_item = atomicAdd(f->fetch, 1u);
+    }
+    P::template build<BLOCK>(m, tb);
+    if (tid < S) s_scale[tid] = a.scale[tid];
+    __syncthreads();
+    // the window of this tile: q windows after a.window (buffers swapped when q is odd)
+    uint32_t q = 0;
+    if constexpr (FLOW) {
+        const uint32_t item = s_item;
+        if (item >= f->nwin * f->ntiles) return true;
+        q = item / f->ntiles;
+        tile = (int64_t)(item - q * f->ntiles);
+    }
+    int32_t *const cur = (q & 1u) ? a.nxt : a.cur;
+    int32_t *const nxt = (q & 1u) ? a.cur : a.nxt;
     const int64_t i0 = tile * BLOCK;
     const int64_t i = i0 + tid;
     const int nlive = (int)min((int64_t)BLOCK, (int64_t)a.T - i0);
@@ -610,23 +682,8 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     const size_t Tpad = (size_t)a.Tpad;
     uint32_t bad = 0;
 
-    // Programmatic dependent launch: the next window's grid may start its
-    // blocks as soon as every block of this one has started; they run up to
-    // griddepcontrol.wait below (set-up and the copies of the constant tables)
-    // while this grid drains. Without such a launch both are no-ops.
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-
     // ---- load: the block's tile of every table, by TMA bulk copies into
     // shared memory (rows padded to 16 bytes; the tables are padded to Tpad)
-    if (tid == 0) {
-        nreact = 0;
-        ncalm = 0;
-        next_chunk = 0;
-        mbar_init(&bar, 1);
-    }
-    P::template build<BLOCK>(m, tb);
-    if (tid < S) s_scale[tid] = a.scale[tid];
-    __syncthreads();
     if (tid == 0) {
         const uint32_t n4 = ((uint32_t)nlive + 3u) & ~3u;
         const uint32_t bytes = (uint32_t)S * n4 * 4u + 2u * (uint32_t)nlive * 16u + n4 * 4u +
@@ -643,25 +700,31 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     if (!a.rmask) s_mask[tid] = 0xFFFFFFFFu;
     cnt_all[S * BLOCK + tid] = 1;
     // the counts and the window index come from the previous window: wait for
-    // it to complete (and its memory to be visible)
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // it to complete (and its memory to be visible); in a flow launch, for the
+    // tiles this one depends on
+    bool deps = true;
+    if constexpr (FLOW) {
+        if (q > 0 && tid < 32) deps = flow_deps_wait(*f, (uint32_t)tile, (uint32_t)(a.window + q));
+    } else {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+    }
     {
-        const uint64_t window = a.window + (a.window_base ? *a.window_base : 0ull);
+        const uint64_t window = a.window + q + (a.window_base ? *a.window_base : 0ull);
         c0 = (uint32_t)window;
         c3 = (uint32_t)(window >> 32) & 0x0FFFFFFFu;
     }
     if (tid == 0) {
         const uint32_t n4 = ((uint32_t)nlive + 3u) & ~3u;
-        for (int s = 0; s < S; ++s) bulk_g2s(cnt_all + s * BLOCK, a.cur + s * Tpad + i0, n4 * 4u, &bar);
+        for (int s = 0; s < S; ++s) bulk_g2s(cnt_all + s * BLOCK, cur + s * Tpad + i0, n4 * 4u, &bar);
         // the tile `prefetch` tiles ahead, processed about half a resident
         // wave later, into L2. The last wave's blocks take the next window's first
         // tiles, from the buffer that window reads (lines that this window's
         // atomics still change are only brought into L2, where they land).
         int64_t p0 = i0 + (int64_t)a.prefetch * BLOCK;
-        const int32_t *pc = a.cur;
+        const int32_t *pc = cur;
         if (p0 >= a.T) {
             p0 -= ((int64_t)a.T + BLOCK - 1) / BLOCK * BLOCK;
-            pc = a.nxt;
+            pc = nxt;
         }
         if (a.prefetch > 0 && p0 >= 0 && p0 < a.T) {
             const uint32_t pl = (uint32_t)min((int64_t)BLOCK, (int64_t)a.T - p0);
@@ -678,14 +741,15 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     // barrier; then every thread observes the completed phase itself
     bool arrived = true;
     if (tid == 0) arrived = mbar_wait_bounded(&bar, 0);
-    if (__syncthreads_or(!arrived)) {
-        // the copies did not land in time: report, let them finish (bounded), skip the window
+    if (__syncthreads_or(!arrived || !deps)) {
+        // the copies did not land in time (or the tiles this one depends on did
+        // not finish): report, let the copies finish (bounded), skip the window
         if (tid == 0) {
-            atomicOr(a.err, 4u);
-            mbar_wait_bounded(&bar, 0);
+            atomicOr(a.err, (arrived ? 0u : 4u) | (deps ? 0u : 8u));
+            if (!arrived) mbar_wait_bounded(&bar, 0);
         }
         __syncthreads();
-        return;
+        return false;
     }
     mbar_try_wait(&bar, 0);  // completed: returns at once
     // `cur` receives the window after next: zero its non-zero entries (an
@@ -693,7 +757,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
     uint32_t nz = 0;
     if (live) {
         int32_t vmin = 0;
-        int32_t *row = a.cur + i;
+        int32_t *row = cur + i;
 #pragma unroll 4
         for (int s = 0; s < S; ++s) {
             const int32_t v = cnt_all[s * BLOCK + tid];
@@ -836,7 +900,7 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
             const int s = __ffs(bw) - 1;
             bw &= bw - 1;
             if ((bm >> s) & 1u)
-                cnt_all[s * BLOCK + t] -= bulk_species(a, s, trial_all[s * tstride + t], s_thr[t],
+                cnt_all[s * BLOCK + t] -= bulk_species(a, nxt, s, trial_all[s * tstride + t], s_thr[t],
                                                        species_R<P>(a, s_scale, s, i0 + t), s_nbr[t], s_tet[t], c0, c3);
         }
         // the chunk's Philox blocks: exclusive prefix of the lanes' block counts
@@ -871,9 +935,9 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
         __syncwarp();
         if (ch < (uint32_t)rchunks) continue;  // diffusion in phase 2
         for (uint32_t item = lane; item < total; item += 32)
-            diffuse_block<BLOCK, P>(a, ww, item, trial_all, tstride, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3, i0);
+            diffuse_block<BLOCK, P>(a, nxt, ww, item, trial_all, tstride, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3, i0);
         __syncwarp();
-        if (valid) apply_remaining<BLOCK, P>(m, a, cnt_all, t, s_nz[t] | touched, i0);
+        if (valid) apply_remaining<BLOCK, P>(m, a, nxt, cnt_all, t, s_nz[t] | touched, i0);
         __syncwarp();
     }
 
@@ -885,15 +949,38 @@ __device__ __forceinline__ void step_tile(const ModelDev &m, const StepArgs &a, 
             const WarpWork &ww = wwork[c];
             const uint32_t total = ww.first[32];
             for (uint32_t item = tid; item < total; item += BLOCK)
-                diffuse_block<BLOCK, P>(a, ww, item, trial_all, tstride, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3, i0);
+                diffuse_block<BLOCK, P>(a, nxt, ww, item, trial_all, tstride, cnt_all, s_thr, s_nbr, s_tet, s_scale, c0, c3, i0);
         }
         __syncthreads();
         for (int c = tid >> 5; c < rchunks; c += BLOCK / 32) {
             const int t = wwork[c].tet[lane];
-            if (t >= 0) apply_remaining<BLOCK, P>(m, a, cnt_all, t, s_nz[t] | wwork[c].touched[lane], i0);
+            if (t >= 0) apply_remaining<BLOCK, P>(m, a, nxt, cnt_all, t, s_nz[t] | wwork[c].touched[lane], i0);
         }
     }
     if (bad) atomicOr(a.err, bad);
+    if constexpr (FLOW) {
+        // publish: every thread's writes of this tile come before the release
+        __syncthreads();
+        if (tid == 0) st_release_gpu(f->tile_done + tile, (uint32_t)(a.window + q + 1));
+    }
+    return true;
+}
+
+// Full windows of one simulation in one launch of nwin x ntiles blocks. Each
+// block takes the next item (window q, tile t), q-major, from a counter. The
+// item (q, t) with q > 0 waits until every tile that shares a face with t,
+// and t itself, has finished window q - 1: the counts t reads are then
+// complete (every atomic that adds into them has landed), and the entries of
+// the buffer t adds into have been read and zeroed by their own tiles. Those
+// are all the dependencies of a window's tile (Algorithm 1: a tet's new
+// counts come from itself and its face neighbours only), so a window's first
+// tiles start while the previous window's last tiles still run, with no
+// grid-wide boundary between windows. An item waits only on items taken
+// before it, which running blocks hold, so the items complete whatever the
+// number of resident blocks.
+template <int BLOCK, int RM, class P>
+__device__ __forceinline__ void flow_tiles(const ModelDev &m, const StepArgs &a, const FlowArgs &f) {
+    step_tile<BLOCK, RM, P, true>(m, a, 0, &f);
 }
 
 // One block of a batched launch: the member named by work[blockIdx.x] copies

@@ -1,0 +1,133 @@
+"""GPU tests of the flow launch form: a run's consecutive full windows in one
+launch, in which each tile of a window starts once the tiles holding its
+face neighbours (and itself) have finished the previous window. It must give
+the oracle's bits and the window launches' bits across tile counts, ragged
+tails, block sizes, buffer parities, trial modes, leave laws and masks; the
+tuning that picks the form must keep the bits; and its bounded dependency
+wait must give up without a fault."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import END
+from paper_1610_02258_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, min(32, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_02258_gb300.build import build
+    build()
+    from paper_1610_02258_gb300 import capi as c
+    return c
+
+
+def _both(capi, w, t_ends, masks=None, occ=oracle.OCC, leave=0, **kw):
+    g = capi.Simulation(w.verts, w.tets, w.model, w.seed, occupancy=occ, leave_law=leave, **kw)
+    g.set_counts(w.counts)
+    o = oracle.OracleSim(w.verts, w.tets, w.model, seed=w.seed, occ=occ, prec=32, leave=leave)
+    o.set_counts(w.counts)
+    for r, m in (masks or {}).items():
+        g.set_reac_mask(r, m)
+        o.set_reac_mask(r, m)
+    for t in np.atleast_1d(t_ends):
+        g.run(t)
+        o.run(t, threads=THREADS)
+        assert g.windows == o.windows
+        assert np.array_equal(g.get_counts(), o.get_counts()), t
+    return g, o
+
+
+def test_flow_wait_completes_and_times_out(capi):
+    capi.steps_debug_flow_wait(True, 1 << 24)           # every listed tile has finished: no error
+    for limit in (1 << 12, 1 << 20):
+        with pytest.raises(capi.StepsError) as e:
+            capi.steps_debug_flow_wait(False, limit)    # one never finishes: the limit runs out
+        assert e.value.code == -6 and "did not complete" in str(e.value)
+    with pytest.raises(capi.StepsError) as e:
+        capi.steps_debug_flow_wait(False, 0)
+    assert e.value.code == -1
+    # the device is still usable: a flow run equals the oracle
+    _both(capi, I.config2(nx=4, t_end=2e-3), [2e-3], specialize=1, flow=True)
+
+
+@pytest.mark.parametrize("which", ["box", "dendrite", "cuboid"])
+def test_flow_bit_exact(capi, which):
+    """Flow launches against the oracle: the 10-species network on a box of
+    41,616 tets (163 tiles, ragged last tile) over stops that leave odd and
+    even numbers of full windows (buffer parity across launches); the calcium
+    network on a small dendrite with its masked zero-order influx; the
+    cuboid (8 tiles)."""
+    if which == "box":
+        w, masks, t_ends = I.config2(nx=24, t_end=4e-3), {}, [0.21e-3 * 3 + 1e-6, 1.9e-3, 4e-3]
+    elif which == "dendrite":
+        w = I.config3(h=0.5e-6, t_end=0.2e-3)
+        masks, t_ends = w.reac_masks, [0.07e-3, 0.2e-3]
+    else:
+        w, masks, t_ends = I.config1(), {}, [3e-3, 10e-3]
+    g, o = _both(capi, w, t_ends, masks=masks, specialize=1, flow=True)
+    assert g.specialized and g.flow[0]
+    assert o.events > 0
+
+
+@pytest.mark.parametrize("mode", ["exp", "end"])
+def test_flow_other_modes_bit_exact(capi, mode):
+    w = I.config2(nx=12, t_end=3e-3)
+    kw = {"leave": oracle.EXP} if mode == "exp" else {"occ": END}
+    g, _ = _both(capi, w, [1.3e-3, w.t_end], specialize=1, flow=True, **kw)
+    assert g.flow[0]
+
+
+@pytest.mark.parametrize("block", [64, 128, 512])
+def test_flow_block_sizes_equal_window_launches(capi, block):
+    w = I.config2(nx=10, t_end=3e-3)
+    out = []
+    for flow in (True, False):
+        g = capi.from_workload(w, specialize=1, flow=flow, block=block)
+        g.run(w.t_end)
+        out.append(g.get_counts())
+        assert g.flow[0] == flow
+        g.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_flow_tuning_keeps_the_bits_full_size(capi):
+    """The benchmark box at full size: the default form (tuned on the first
+    run's own windows), forced flow and forced window launches all give the
+    same counts over the 20 ms run, and the oracle's."""
+    w = I.config2()
+    res = {}
+    for flow in (None, True, False):
+        g = capi.from_workload(w, flow=flow)
+        g.run(w.t_end)
+        res[flow] = g.get_counts()
+        active, ms = g.flow
+        if flow is None:
+            assert ms[0] > 0 and ms[1] > 0  # both forms timed
+            assert active == (ms[1] < 0.98 * ms[0])
+        else:
+            assert active == flow and ms == [0.0, 0.0]
+        g.close()
+    assert np.array_equal(res[None], res[True]) and np.array_equal(res[True], res[False])
+    o = oracle.from_workload(w, prec=32)
+    o.run(w.t_end, threads=THREADS)
+    assert np.array_equal(res[True], o.get_counts())
+
+
+def test_flow_dendrite_full_size_equals_window_launches(capi):
+    w = I.config3(t_end=0.5e-3)
+    out = []
+    for flow in (True, False):
+        g = capi.from_workload(w, flow=flow)
+        g.run(w.t_end)
+        out.append(g.get_counts())
+        g.close()
+    assert np.array_equal(out[0], out[1])

@@ -22,11 +22,13 @@ def capi():
     return c
 
 
-def test_influx_schedule_and_recording_match_the_oracle(capi):
+@pytest.mark.parametrize("flow", [None, True])
+def test_influx_schedule_and_recording_match_the_oracle(capi, flow):
+    """flow = True: the model-specialised kernel, full windows as flow launches."""
     import torch
     w = I.config3(h=0.5e-6, t_end=1e-3)  # ~30k-tet dendrite, 20 species, masked influx
     influx = w.model.n_reac - 1
-    g = capi.from_workload(w)
+    g = capi.from_workload(w, specialize=1 if flow else 0, flow=flow)
     o = oracle.from_workload(w, prec=32)
     tau = g.tau
     assert g.tau == o.tau
