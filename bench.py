@@ -3,9 +3,12 @@
 
 Workload: jittered 100x10x10 um box of 294,780 tets, random 10-species /
 20-reaction network, densities 1-100 /um^3, tau = 0.203 ms. One benchmark
-step = one steps_run call advancing the simulation by 20 ms (98 full windows
-and one shortened window = 99 launches of the fused step kernel, replayed
-from CUDA graphs). Metric: tet-updates/s = tets x windows / time.
+step = one steps_run call advancing the simulation by 20 ms: 98 full windows
+and one shortened window. The full windows run in the launch form the
+simulation's first run picked by timing both (a flow launch: all 98 windows
+in one launch, each tile starting when its neighbour tiles finished the
+previous window; or one launch per window, replayed from CUDA graphs); the
+shortened window is one launch. Metric: tet-updates/s = tets x windows / time.
 
   value     device time (CUDA events on the simulation's stream) of K steps,
             state resident in HBM; L2 flushed (256 MiB write) before each step,
@@ -13,9 +16,10 @@ from CUDA graphs). Metric: tet-updates/s = tets x windows / time.
   e2e       the same metric through the public C ABI with host buffers:
             steps_set_counts_all (H2D), steps_run, steps_get_counts_all (D2H),
             wall clock per step.
-  roofline  the step kernel. The box's working set sits in L2 and the kernel
+  roofline  the step kernel, per window (a flow launch's ncu counts divided
+            by its windows). The box's working set sits in L2 and the kernel
             is bound by instruction issue: bound "alu", warp instructions
-            (ncu count per launch) per second against 152 SMs x 4 schedulers
+            (ncu count per window) per second against 152 SMs x 4 schedulers
             x 1 warp instruction per cycle x the sampled SM clock. Beside it,
             `hbm`: algorithmic bytes per launch / average launch time against
             the measured copy bandwidth, on 8S + 52 bytes per tet-update (FP64
@@ -139,7 +143,22 @@ def profile_traffic(name: str):
         return None
     if kv.get("kernel_sources_sha256_16", "").strip() != kernel_sources_hash():
         return None
-    return {k.strip(): int(v) for k, v in kv.items() if k.strip() != "kernel_sources_sha256_16"}
+    tr = {k.strip(): int(v) for k, v in kv.items() if k.strip() != "kernel_sources_sha256_16"}
+    # a flow launch holds several windows: the roofline works per window
+    wpl = tr.get("windows_per_launch", 1)
+    if wpl > 1:
+        for k in ("bytes_per_launch", "read_bytes", "write_bytes", "warp_instructions_per_launch"):
+            if k in tr:
+                tr[k] = tr[k] // wpl
+    return tr
+
+
+def launch_form(sim):
+    """(profile prefix, config keys) of a plain simulation's launch form."""
+    active, tune = sim.flow
+    keys = {"launch_form": "flow" if active else "window launches",
+            "flow_tuning_ms_per_window": {"window_launches": tune[0], "flow": tune[1]} if tune[0] > 0 else None}
+    return ("flow_kernel" if active else "step_kernel"), keys
 
 
 def issue_roofline(tr, kernel_s: float, sm_mhz):
@@ -155,7 +174,7 @@ def issue_roofline(tr, kernel_s: float, sm_mhz):
     peak = sms * 4 * mhz * 1e6
     achieved = tr["warp_instructions_per_launch"] / kernel_s
     return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp-inst/s", "frac": achieved / peak,
-            "warp_instructions_per_launch": tr["warp_instructions_per_launch"], "sm_mhz": mhz,
+            "warp_instructions_per_window": tr["warp_instructions_per_launch"], "sm_mhz": mhz,
             "note": "instruction count from the ncu capture in profiles/, time from this run"}
 
 
@@ -259,7 +278,7 @@ def roofline(S: int, masked: bool, tets: int, kernel_s: float, peak: float, peak
         out = {"bound": "alu", "achieved": iss["achieved"], "peak": iss["peak"], "unit": "warp-inst/s",
                "frac": iss["frac"], "traffic": hbm["traffic"],
                "peak_source": f"SMs x 4 schedulers x 1 warp instruction/cycle x {iss['sm_mhz']:.0f} MHz (sampled)",
-               "warp_instructions_per_launch": iss["warp_instructions_per_launch"], "kernel_us_avg": kernel_s * 1e6,
+               "warp_instructions_per_window": iss["warp_instructions_per_window"], "kernel_us_avg": kernel_s * 1e6,
                "note": "working set in L2; bound by instruction issue (ncu issue slots and stalls in profiles/)",
                "hbm": hbm}
         return out
@@ -370,9 +389,10 @@ def measure_dendrite(args, capi, I, torch, peak):
     windows = w1 - w0
     S = w.model.n_species
     kernel_s = (ms / 1e3) / windows
-    tr = profile_traffic("step_kernel_dendrite")
+    prefix, form_keys = launch_form(sim)
+    tr = profile_traffic(prefix + "_dendrite")
     out = {"value": w.n_tets * windows / (ms / 1e3), "unit": UNIT, "workload": w.name, "tets": w.n_tets,
-           "form": "plain", "kernel": "specialised" if sim.specialized else "generic",
+           "form": "plain", "kernel": "specialised" if sim.specialized else "generic", **form_keys,
            "species": S, "reactions": w.model.n_reac, "tau_us": sim.tau * 1e6, "sim_ms_per_step": args.dendrite_ms,
            "windows_per_step": windows / steps, "ms_per_step": ms / steps, "steps": steps,
            "roofline": roofline(S, bool(w.reac_masks), w.n_tets, kernel_s, peak, "measured", tr, None, False),
@@ -521,7 +541,7 @@ def measure_sweeps(args, capi, I, torch):
         counts = np.ascontiguousarray(w.counts, np.int32)
         sim = capi.from_workload(w, cuda_stream=stream.cuda_stream)
         sim.set_counts(counts)
-        sim.run(sim.time + 2e-3)  # warm
+        sim.run(sim.time + 20e-3)  # warm: the first run also picks the launch form
         ms, wins = 0.0, 0
         for _ in range(2):
             sim.set_counts(counts)
@@ -536,7 +556,7 @@ def measure_sweeps(args, capi, I, torch):
             wins += sim.windows - w0
         out = {"tets": w.n_tets, "molecules_per_tet": float(counts.sum()) / w.n_tets, "tau_us": sim.tau * 1e6,
                "us_per_window": 1e3 * ms / wins, "value": w.n_tets * wins / (ms / 1e3), "unit": UNIT,
-               "kernel": "specialised" if sim.specialized else "generic"}
+               "kernel": "specialised" if sim.specialized else "generic", **launch_form(sim)[1]}
         sim.close()
         return out
 
@@ -602,7 +622,7 @@ def run_ours(args):
     else:
         w = I.config2(seed=replica_seed(rank))
     stream = torch.cuda.current_stream()
-    sim = capi.from_workload(w, cuda_stream=stream.cuda_stream)
+    sim = capi.from_workload(w, cuda_stream=stream.cuda_stream, flow={"auto": None, "on": True, "off": False}[args.flow])
     tau = sim.tau
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     t_step = args.sim_ms * 1e-3 if args.sim_ms > 0 else w.t_end
@@ -669,7 +689,8 @@ def run_ours(args):
     S = w.model.n_species
     kernel_s = (ms / 1e3) / windows
     peak, peak_kind = _peaks()
-    tr = profile_traffic("step_kernel_dendrite" if args.workload == "dendrite" else "step_kernel_config2")
+    prefix, form_keys = launch_form(sim)
+    tr = profile_traffic(prefix + ("_dendrite" if args.workload == "dendrite" else "_config2"))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
@@ -677,7 +698,7 @@ def run_ours(args):
         "config": {"workload": w.name, "tets": w.n_tets, "species": S, "reactions": w.model.n_reac,
                    "tau_ms": tau * 1e3, "sim_ms_per_step": t_step * 1e3,
                    "windows_per_step": windows / args.steps, "form": "plain",
-                   "kernel": "specialised" if sim.specialized else "generic",
+                   "kernel": "specialised" if sim.specialized else "generic", **form_keys,
                    "l2": "flushed before each timed step (256 MiB write, outside the events)",
                    "step": "steps_run over sim_ms_per_step from the initial counts (reset outside the events)",
                    "parallelism": f"replicas{world}"},
@@ -716,6 +737,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--batch-replicates", type=int, default=256)
+    ap.add_argument("--flow", choices=["auto", "on", "off"], default="auto",
+                    help="launch form of the plain run's full windows: tuned on the first run (auto), flow launches "
+                         "(on) or window launches (off)")
     ap.add_argument("--served-jobs", type=int, default=1000)
     ap.add_argument("--sweep", action="store_true",
                     help="add the density (0.1x/1x/10x) and mesh-size (8/17/26 cubes across) sweeps of the box")
