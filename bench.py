@@ -155,10 +155,11 @@ def profile_traffic(name: str):
 
 def launch_form(sim):
     """(profile prefix, config keys) of a plain simulation's launch form."""
-    active, tune = sim.flow
-    keys = {"launch_form": "flow" if active else "window launches",
-            "flow_tuning_ms_per_window": {"window_launches": tune[0], "flow": tune[1]} if tune[0] > 0 else None}
-    return ("flow_kernel" if active else "step_kernel"), keys
+    block, tune = sim.flow
+    keys = {"launch_form": f"flow ({block}-tet tiles)" if block else "window launches",
+            "flow_tuning_ms_per_window": {"window_launches": tune[0], "flow": tune[1], "flow_512": tune[2]}
+            if tune[0] > 0 else None}
+    return (f"flow{block}_kernel" if block else "step_kernel"), keys
 
 
 def issue_roofline(tr, kernel_s: float, sm_mhz):
@@ -622,7 +623,8 @@ def run_ours(args):
     else:
         w = I.config2(seed=replica_seed(rank))
     stream = torch.cuda.current_stream()
-    sim = capi.from_workload(w, cuda_stream=stream.cuda_stream, flow={"auto": None, "on": True, "off": False}[args.flow])
+    sim = capi.from_workload(w, cuda_stream=stream.cuda_stream, block=args.block,
+                             flow={"auto": None, "on": True, "off": False}[args.flow])
     tau = sim.tau
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     t_step = args.sim_ms * 1e-3 if args.sim_ms > 0 else w.t_end
@@ -737,6 +739,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--batch-replicates", type=int, default=256)
+    ap.add_argument("--block", type=int, default=256, choices=[64, 128, 256, 512],
+                    help="tile size (threads per block) of the plain run")
     ap.add_argument("--flow", choices=["auto", "on", "off"], default="auto",
                     help="launch form of the plain run's full windows: tuned on the first run (auto), flow launches "
                          "(on) or window launches (off)")

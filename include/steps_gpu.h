@@ -78,9 +78,10 @@ typedef struct steps_options {
                             Flow: one launch for all of them, in which each tile of a window starts as soon as
                             the tiles holding its face neighbours have finished the previous window. Window
                             launches: one launch per window (graph replay as use_graph says). 0 (default): the
-                            first run with at least 48 full windows times both on its own windows and keeps the
-                            faster (steps_sim_flow reports it); 1: flow; -1: window launches. The results are
-                            the same bits in every form. */
+                            first run with at least 72 full windows times, on its own windows, window launches,
+                            flow launches of `block`-tet tiles and (when block < 512) of 512-tet tiles, and keeps
+                            the fastest (steps_sim_flow reports it); 1: flow at `block`; -1: window launches.
+                            The results are the same bits in every form. */
     int32_t reserved[1]; /* set to 0 */
 } steps_options;
 
@@ -214,10 +215,11 @@ int steps_run_record(steps_sim *sim, double t_end, double dt_rec, int32_t n_spec
  * results bit for bit; the specialised one takes fewer instructions. */
 int steps_sim_specialized(const steps_sim *sim, int32_t *specialized);
 
-/* *active = 1 when the simulation's full windows run as flow launches (steps_options.flow), else 0.
- * tune_ms (may be NULL): [2] ms per window of window launches and of flow launches measured by the
- * tuning run (0 before it, or without one). */
-int steps_sim_flow(const steps_sim *sim, int32_t *active, float *tune_ms);
+/* *flow_block = the tile size (threads per block) of the flow launches the simulation's full windows
+ * run as (steps_options.flow), or 0 when they run as window launches. tune_ms (may be NULL): [3] ms per
+ * window measured by the tuning run for window launches, flow launches at the simulation's block size
+ * and flow launches of 512-tet tiles (0 for a form not timed, and before the tuning run). */
+int steps_sim_flow(const steps_sim *sim, int32_t *flow_block, float *tune_ms);
 
 /* Tets and species of a simulation (either output may be NULL). */
 int steps_sim_shape(const steps_sim *sim, int64_t *nt, int32_t *n_species);

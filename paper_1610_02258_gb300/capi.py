@@ -267,11 +267,12 @@ def steps_sim_specialized(sim):
 
 
 def steps_sim_flow(sim):
-    """(active, [ms per window of window launches, of flow launches] from the tuning run)."""
+    """(tile size of the flow launches, 0 for window launches; [ms per window of window
+    launches, flow at the simulation's block, flow at 512] from the tuning run)."""
     v = ctypes.c_int32(0)
-    ms = (ctypes.c_float * 2)()
+    ms = (ctypes.c_float * 3)()
     _check(lib.steps_sim_flow(sim, ctypes.byref(v), ms))
-    return bool(v.value), [float(ms[0]), float(ms[1])]
+    return int(v.value), [float(x) for x in ms]
 
 
 def steps_get_time(sim):
@@ -536,7 +537,7 @@ class Simulation:
 
     @property
     def flow(self):
-        """(full windows run as flow launches, tuning ms per window [window launches, flow launches])."""
+        """(tile size of the flow launches or 0, tuning ms per window [window launches, flow, flow at 512])."""
         return steps_sim_flow(self._sim)
 
     @property

@@ -34,7 +34,7 @@ struct steps_model {
 namespace {
 
 constexpr int kGraphWindows = 16;  // full windows per captured graph (even: buffer parity is restored)
-constexpr int64_t kFlowTuneWindows = 48;  // windows the launch-form tuning takes (3 rounds of 2 groups)
+constexpr int64_t kFlowTuneWindows = 72;  // windows the launch-form tuning takes (3 rounds of up to 3 groups)
 
 __global__ void scatter_to_device_order(const int32_t *src, int64_t nt, int32_t S, const int32_t *inv_perm,
                                         int32_t *dst, size_t Tpad) {
@@ -108,16 +108,23 @@ struct steps_sim {
     uint32_t scale_full[kMaxSpecies] = {};
     // graphs of kGraphWindows full windows, one per starting buffer
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    // flow launches (a run's full windows in one persistent launch): each tile's
-    // neighbour tiles (tiles of opt.block tets in device order, CSR), the tiles'
-    // finished-window words and the item counter (d_flow[ntiles])
-    int32_t *d_tnb_off = nullptr;
-    int32_t *d_tnb = nullptr;
-    uint32_t *d_flow = nullptr;
-    int64_t ntiles = 0;
-    size_t flow_bytes = 0;
-    int flow_pick = -1;          // flow = 0 (auto): -1 not yet timed, 0 window launches, 1 flow launches
-    float flow_ms[2] = {0.f, 0.f};  // tuning: ms per window of window launches and of flow launches
+    // flow launches (a run's full windows in one launch), per block size: [0]
+    // the simulation's, [1] 512 (a tuning candidate when the block is smaller).
+    // Each holds its step kernel, every tile's neighbour tiles (tiles of
+    // `block` tets in device order, CSR), the tiles' finished-window words and
+    // the item counter (d_flow[ntiles]).
+    struct Flow {
+        void *spec = nullptr;
+        int block = 0;
+        bool tried = false;
+        int32_t *d_tnb_off = nullptr;
+        int32_t *d_tnb = nullptr;
+        uint32_t *d_flow = nullptr;
+        int64_t ntiles = 0;
+        size_t bytes = 0;
+    } flow[2];
+    int flow_pick = -1;  // flow = 0 (tuned): -1 not yet timed, 0 window launches, 1 + k flow launches of flow[k]
+    float flow_ms[3] = {0.f, 0.f, 0.f};  // tuning: ms per window of window launches, flow[0], flow[1]
 
     double time() const { return k_grid == 0 ? t_base : t_base + (double)k_grid * tab.tau; }
 
@@ -139,16 +146,23 @@ struct steps_sim {
         cudaFree(d_trial);
         cudaFree(d_leave[0]);
         cudaFree(d_leave[1]);
-        cudaFree(d_tnb_off);
-        cudaFree(d_tnb);
-        cudaFree(d_flow);
+        for (Flow &f : flow) {
+            cudaFree(f.d_tnb_off);
+            cudaFree(f.d_tnb);
+            cudaFree(f.d_flow);
+        }
     }
 
-    // the flow kernel's tables (once): tile t lists itself and every tile
-    // holding a face neighbour of one of its tets
-    int ensure_flow() {
-        if (d_flow) return STEPS_OK;
-        const int64_t B = opt.block;
+    // flow[k]'s kernel and tables (once): tile t lists itself and every tile
+    // holding a face neighbour of one of its tets. flow[1]'s kernel is
+    // compiled here; if that fails, flow[1].spec stays null (no candidate).
+    int ensure_flow(int k) {
+        Flow &fl = flow[k];
+        if (fl.d_flow || fl.tried) return STEPS_OK;
+        fl.tried = true;
+        const int64_t B = k == 0 ? opt.block : 512;
+        void *sp = k == 0 ? spec : spec_kernel(model, 512, nullptr);
+        if (!sp) return STEPS_OK;
         const int64_t nt = (T + B - 1) / B;
         std::vector<int32_t> off, nb, tmp;
         try {
@@ -170,22 +184,24 @@ struct steps_sim {
             set_error("flow tables: out of host memory");
             return STEPS_ERR_OOM;
         }
-        if (!cuda_ok(cudaMalloc((void **)&d_tnb_off, off.size() * 4), "flow tables") ||
-            !cuda_ok(cudaMalloc((void **)&d_tnb, nb.size() * 4), "flow tables") ||
-            !cuda_ok(cudaMalloc((void **)&d_flow, ((size_t)nt + 1) * 4), "flow tables")) {
-            cudaFree(d_tnb_off);
-            cudaFree(d_tnb);
-            cudaFree(d_flow);
-            d_tnb_off = d_tnb = nullptr;
-            d_flow = nullptr;
+        if (!cuda_ok(cudaMalloc((void **)&fl.d_tnb_off, off.size() * 4), "flow tables") ||
+            !cuda_ok(cudaMalloc((void **)&fl.d_tnb, nb.size() * 4), "flow tables") ||
+            !cuda_ok(cudaMalloc((void **)&fl.d_flow, ((size_t)nt + 1) * 4), "flow tables")) {
+            cudaFree(fl.d_tnb_off);
+            cudaFree(fl.d_tnb);
+            cudaFree(fl.d_flow);
+            fl.d_tnb_off = fl.d_tnb = nullptr;
+            fl.d_flow = nullptr;
             return STEPS_ERR_OOM;
         }
-        if (!cuda_ok(cudaMemcpy(d_tnb_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice), "flow tables") ||
-            !cuda_ok(cudaMemcpy(d_tnb, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice), "flow tables") ||
-            !cuda_ok(cudaMemset(d_flow, 0, ((size_t)nt + 1) * 4), "flow tables"))
+        if (!cuda_ok(cudaMemcpy(fl.d_tnb_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice), "flow tables") ||
+            !cuda_ok(cudaMemcpy(fl.d_tnb, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice), "flow tables") ||
+            !cuda_ok(cudaMemset(fl.d_flow, 0, ((size_t)nt + 1) * 4), "flow tables"))
             return STEPS_ERR_CUDA;
-        ntiles = nt;
-        flow_bytes = (off.size() + nb.size() + (size_t)nt + 1) * 4;
+        fl.spec = sp;
+        fl.block = (int)B;
+        fl.ntiles = nt;
+        fl.bytes = (off.size() + nb.size() + (size_t)nt + 1) * 4;
         return STEPS_OK;
     }
 
@@ -298,7 +314,7 @@ struct steps_sim {
         return rc;
     }
 
-    // n full windows: flow launches or window launches (both give the same bits)
+    // n full windows: flow launches or window launches (all give the same bits)
     int full_windows(int64_t n) {
         if (spec && opt.flow == 0 && flow_pick < 0 && n >= kFlowTuneWindows) {
             int64_t used = 0;
@@ -306,18 +322,30 @@ struct steps_sim {
             if (rc) return rc;
             n -= used;
         }
-        if (spec && n >= 2 && (opt.flow == 1 || (opt.flow == 0 && flow_pick == 1))) return flow_windows(n);
-        return window_launches(n);
+        int k = -1;
+        if (spec && n >= 2) {
+            if (opt.flow == 1) k = 0;
+            else if (opt.flow == 0 && flow_pick >= 1) k = flow_pick - 1;
+        }
+        return k >= 0 ? flow_windows(n, k) : window_launches(n);
     }
 
-    // The first run with enough full windows times both launch forms on
-    // alternating groups of windows (after one warm group of each, so that
-    // one-time costs and the state's slow drift do not decide) and keeps the
-    // flow launches when they are more than 2 % faster. The windows taken
-    // are ordinary windows of the run.
+    // The first run with enough full windows times the launch forms on
+    // alternating groups of windows: window launches, flow launches at the
+    // simulation's block size and, when that is below 512, flow launches of
+    // 512-tet tiles. One warm round, so that one-time costs do not decide,
+    // then two timed rounds, so that the state's slow drift cancels. The
+    // fastest flow form is kept when it is more than 2 % faster than window
+    // launches. The windows taken are ordinary windows of the run.
     int tune_flow(int64_t *used) {
-        int rc = ensure_flow();
+        int rc = ensure_flow(0);
+        if (!rc && opt.block < 512) rc = ensure_flow(1);
         if (rc) return rc;
+        const int nc = flow[0].spec ? (flow[1].spec ? 3 : 2) : 1;
+        if (nc == 1) {
+            flow_pick = 0;
+            return STEPS_OK;
+        }
         cudaEvent_t e[4] = {};
         for (auto &ev : e)
             if (!cuda_ok(cudaEventCreate(&ev), "flow tuning event")) {
@@ -325,30 +353,29 @@ struct steps_sim {
                     if (x) cudaEventDestroy(x);
                 return STEPS_ERR_CUDA;
             }
-        float tot[2] = {0.f, 0.f};
-        const int64_t g = kFlowTuneWindows / 6;  // windows per group: warm, then two timed rounds
+        float tot[3] = {0.f, 0.f, 0.f};
+        const int64_t g = kFlowTuneWindows / (3 * nc);  // windows per group
         for (int round = 0; round < 3 && rc == STEPS_OK; ++round) {
-            if (!cuda_ok(cudaEventRecord(e[0], stream), "flow tuning")) rc = STEPS_ERR_CUDA;
-            if (!rc) rc = window_launches(g);
-            if (!rc && !cuda_ok(cudaEventRecord(e[1], stream), "flow tuning")) rc = STEPS_ERR_CUDA;
-            if (!rc) rc = flow_windows(g);
-            if (!rc && !cuda_ok(cudaEventRecord(e[2], stream), "flow tuning")) rc = STEPS_ERR_CUDA;
-            float a = 0.f, b = 0.f;
-            if (!rc && (!cuda_ok(cudaEventSynchronize(e[2]), "flow tuning") ||
-                        !cuda_ok(cudaEventElapsedTime(&a, e[0], e[1]), "flow tuning") ||
-                        !cuda_ok(cudaEventElapsedTime(&b, e[1], e[2]), "flow tuning")))
-                rc = STEPS_ERR_CUDA;
-            if (!rc && round > 0) {
-                tot[0] += a;
-                tot[1] += b;
+            for (int c = 0; c < nc && rc == STEPS_OK; ++c) {
+                if (!cuda_ok(cudaEventRecord(e[c], stream), "flow tuning")) rc = STEPS_ERR_CUDA;
+                if (!rc) rc = c == 0 ? window_launches(g) : flow_windows(g, c - 1);
+                *used += g;
             }
-            *used += 2 * g;
+            if (!rc && !cuda_ok(cudaEventRecord(e[nc], stream), "flow tuning")) rc = STEPS_ERR_CUDA;
+            if (!rc && !cuda_ok(cudaEventSynchronize(e[nc]), "flow tuning")) rc = STEPS_ERR_CUDA;
+            for (int c = 0; c < nc && rc == STEPS_OK; ++c) {
+                float ms = 0.f;
+                if (!cuda_ok(cudaEventElapsedTime(&ms, e[c], e[c + 1]), "flow tuning")) rc = STEPS_ERR_CUDA;
+                else if (round > 0) tot[c] += ms;
+            }
         }
         for (auto &x : e) cudaEventDestroy(x);
         if (rc) return rc;
-        flow_ms[0] = tot[0] / (2.f * (float)g);
-        flow_ms[1] = tot[1] / (2.f * (float)g);
-        flow_pick = tot[1] < 0.98f * tot[0] ? 1 : 0;
+        int best = 1;
+        for (int c = 2; c < nc; ++c)
+            if (tot[c] < tot[best]) best = c;
+        for (int c = 0; c < nc; ++c) flow_ms[c] = tot[c] / (2.f * (float)g);
+        flow_pick = tot[best] < 0.98f * tot[0] ? best : 0;
         return STEPS_OK;
     }
 
@@ -381,24 +408,27 @@ struct steps_sim {
         return STEPS_OK;
     }
 
-    // n full windows through persistent launches of the flow kernel (one per
-    // 2^31 items)
-    int flow_windows(int64_t n) {
-        int rc = ensure_flow();
+    // n full windows through launches of flow[k]'s kernel (one per 2^31 items)
+    int flow_windows(int64_t n, int k) {
+        int rc = ensure_flow(k);
         if (rc) return rc;
+        const Flow &fl = flow[k];
+        if (!fl.spec) return window_launches(n);
+        const int64_t ntiles = fl.ntiles;
+        uint32_t *const d_flow = fl.d_flow;
         const int64_t cap = std::max<int64_t>(1, (int64_t)0x7FFFFFFF / ntiles);
         for (int64_t done = 0; done < n;) {
             const int64_t nw = std::min(n - done, cap);
             if (!cuda_ok(cudaMemsetAsync(d_flow + ntiles, 0, 4, stream), "flow counter")) return STEPS_ERR_CUDA;
             StepArgs a = args(cur, k_total, nullptr, tab.tau, scale_full);
             FlowArgs f;
-            f.tnb_off = d_tnb_off;
-            f.tnb = d_tnb;
+            f.tnb_off = fl.d_tnb_off;
+            f.tnb = fl.d_tnb;
             f.tile_done = d_flow;
             f.fetch = d_flow + ntiles;
             f.nwin = (uint32_t)nw;
             f.ntiles = (uint32_t)ntiles;
-            rc = launch_spec_flow(spec, model.dev, a, f, opt.block, stream);
+            rc = launch_spec_flow(fl.spec, model.dev, a, f, fl.block, stream);
             if (rc) return rc;
             ++launches;
             done += nw;
@@ -680,7 +710,7 @@ int steps_sim_device_bytes(const steps_sim *sim, int64_t *bytes) {
     const int64_t Tpad = sim->Tpad, S = sim->S, T = sim->T;
     *bytes = 2 * S * Tpad * 4 + Tpad * 16 * 2 + Tpad * 4 + 16 + S * T * 4 + (sim->d_orig ? Tpad * 4 + T * 4 : 0) +
              (sim->d_trial ? S * Tpad * 4 : 0) + (sim->d_leave[0] ? 2 * S * Tpad * 4 : 0) +
-             (sim->d_rmask ? Tpad * 4 : 0) + (int64_t)sim->flow_bytes;
+             (sim->d_rmask ? Tpad * 4 : 0) + (int64_t)(sim->flow[0].bytes + sim->flow[1].bytes);
     return STEPS_OK;
 }
 
@@ -979,14 +1009,17 @@ int steps_run_record(steps_sim *sim, double t_end, double dt_rec, int32_t n_spec
     return rc;
 }
 
-int steps_sim_flow(const steps_sim *sim, int32_t *active, float *tune_ms) {
+int steps_sim_flow(const steps_sim *sim, int32_t *flow_block, float *tune_ms) {
     CHECK_NULL(sim, "steps_sim_flow");
-    CHECK_NULL(active, "steps_sim_flow");
-    *active = sim->spec && (sim->opt.flow == 1 || (sim->opt.flow == 0 && sim->flow_pick == 1)) ? 1 : 0;
-    if (tune_ms) {
-        tune_ms[0] = sim->flow_ms[0];
-        tune_ms[1] = sim->flow_ms[1];
+    CHECK_NULL(flow_block, "steps_sim_flow");
+    int k = -1;
+    if (sim->spec) {
+        if (sim->opt.flow == 1) k = 0;
+        else if (sim->opt.flow == 0 && sim->flow_pick >= 1) k = sim->flow_pick - 1;
     }
+    *flow_block = k < 0 ? 0 : k == 0 ? sim->opt.block : 512;
+    if (tune_ms)
+        for (int c = 0; c < 3; ++c) tune_ms[c] = sim->flow_ms[c];
     return STEPS_OK;
 }
 
