@@ -287,17 +287,19 @@ def roofline(S: int, masked: bool, tets: int, kernel_s: float, peak: float, peak
     return hbm
 
 
-def measure_batched(args, capi, I, torch, peak):
+def measure_batched(args, capi, I, torch, peak, flow=False):
     """Batched form: 256 replicates of config-2-style boxes, sizes log-uniform in
     [10k, 300k] tets, distinct seeds, 20 ms per step, one launch per window for
-    all replicates, CUDA-graph replay, autotuned block size."""
+    all replicates, CUDA-graph replay, autotuned block size. flow: one flow
+    launch per L2-sized group of replicates for all full windows of a run
+    (256-tet tiles)."""
     sizes = I.batch_sizes(n=args.batch_replicates)
     t0 = time.perf_counter()
     ws = [I.box_for_tets(int(sz), seed=1000 + j) for j, sz in enumerate(sizes)]
     stream = torch.cuda.current_stream()
     sims = [capi.from_workload(w, cuda_stream=stream.cuda_stream) for w in ws]
     setup_s = time.perf_counter() - t0
-    batch = capi.Batch(sims, block=0, cuda_stream=stream.cuda_stream)
+    batch = capi.Batch(sims, block=256 if flow else 0, cuda_stream=stream.cuda_stream, flow=flow)
     T = np.array([s.nt for s in sims], dtype=np.int64)
     S = ws[0].model.n_species
 
@@ -333,17 +335,19 @@ def measure_batched(args, capi, I, torch, peak):
     achieved = units * (8 * S + 52) / (ms / 1e3) / 1e9
     achieved36 = units * (8 * S + 36) / (ms / 1e3) / 1e9
     blk, _, tune = batch.info
-    tr = profile_traffic("step_kernel_batch_config4_32rep")
+    tr = profile_traffic("step_kernel_batch_flow_config4_32rep" if flow else "step_kernel_batch_config4_32rep")
     # captured on 32 replicates (units_per_launch tets); traffic grows with the tets of a launch
     traffic = tr["bytes_per_launch"] / tr["units_per_launch"] * float(T.sum()) if tr else None
     out = {"value": units / (ms / 1e3), "unit": UNIT, "replicates": len(sims), "tets": int(T.sum()),
            "kernel": "specialised" if batch.specialized else "generic",
+           "launch_form": "flow per L2-sized group of replicates" if flow else "one launch per window",
            "tets_min": int(T.min()), "tets_max": int(T.max()), "ms_per_step": ms / steps, "steps": steps,
            "windows_per_step_max": launches / steps, "block": blk, "autotune_ms_per_window": tune,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "bytes_per_tet_update": 8 * S + 52, "achieved_fixed_point": achieved36,
                         "frac_fixed_point": achieved36 / peak, "bytes_per_tet_update_fixed_point": 8 * S + 36,
-                        "traffic": traffic, "traffic_note": "ncu DRAM bytes per launch on 32 replicates, scaled by tets",
+                        "traffic": traffic,
+                        "traffic_note": "ncu DRAM bytes per window on 32 replicates, scaled by tets",
                         "traffic_per_tet_update": (tr["bytes_per_launch"] / tr["units_per_launch"]) if tr else None},
            "setup_s": setup_s, "l2": "working set > L2; also flushed before each step",
            "step": "one batched run of 20 ms per member from its initial counts (reset outside the events)"}
@@ -719,6 +723,8 @@ def run_ours(args):
                          "dendrite_influx_recording": (measure_dendrite_recording(args, capi, I, torch)
                                                        if args.dendrite_ms > 0 else None),
                          "batched": measure_batched(args, capi, I, torch, peak) if args.batch_replicates > 0 else None,
+                         "batched_flow": (measure_batched(args, capi, I, torch, peak, flow=True)
+                                          if args.batch_replicates > 0 else None),
                          "served": measure_served(args, capi, I) if args.served_jobs > 0 else None}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, 4 * args.cpu_windows, max(5, args.cpu_windows // 4))

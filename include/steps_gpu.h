@@ -242,7 +242,13 @@ typedef struct steps_batch_options {
                             may differ), they hold at least 65,536 tets together and NVRTC is available
                             (default), 1 = always (creation fails with STEPS_ERR_ARG if the members differ in
                             structure, the first run with STEPS_ERR_CUDA if it cannot be built), -1 = never */
-    int32_t reserved[5]; /* set to 0 */
+    int32_t flow;        /* 0 (default): one launch per window for all members. 1: on the specialised batched
+                            kernel, a run's full windows go through one launch per group of consecutive members
+                            whose tables fit in about half of L2, in which each tile of a window starts once the
+                            tiles holding its face neighbours have finished the previous window. The members'
+                            results are the same bits; the groups' windows run from L2 (far fewer DRAM bytes),
+                            at a few per cent lower throughput on an issue-bound batch. */
+    int32_t reserved[4]; /* set to 0 */
 } steps_batch_options;
 
 void steps_batch_options_default(steps_batch_options *opt);

@@ -53,7 +53,7 @@ class steps_options(ctypes.Structure):
 
 class steps_batch_options(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("specialize", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("flow", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class steps_server_options(ctypes.Structure):
@@ -362,12 +362,13 @@ def steps_batch_info(batch):
 class Batch:
     """A batch over existing Simulation objects (kept alive by this object)."""
 
-    def __init__(self, sims, block=0, use_graph=True, cuda_stream=None, specialize=0):
+    def __init__(self, sims, block=0, use_graph=True, cuda_stream=None, specialize=0, flow=False):
         self.sims = list(sims)
         opt = steps_batch_options_default()
         opt.block = block
         opt.use_graph = 1 if use_graph else 0
         opt.specialize = int(specialize)
+        opt.flow = 1 if flow else 0
         self._h = steps_batch_create([s._sim for s in self.sims], opt, cuda_stream)
 
     def run(self, t_end):

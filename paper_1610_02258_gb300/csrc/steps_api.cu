@@ -1229,6 +1229,19 @@ struct steps_batch {
     void *spec[4] = {};         // per block size, compiled on first use (before any capture)
     std::string spec_why;
     std::vector<float> tune_ms;  // autotune timings per candidate block (ms per window)
+    bool flow = false;           // full windows of member groups as flow launches (specialised kernel)
+    // flow launches, per block size: the neighbour tiles of every work entry
+    // (CSR over work indices), the entries' finished-window words followed by
+    // the item counter, and the groups: consecutive members whose tables fit
+    // in about half of L2 (at least one member each), so that a group's
+    // windows run from L2
+    struct Flow {
+        int32_t *d_tnb_off = nullptr;
+        int32_t *d_tnb = nullptr;
+        uint32_t *d_flow = nullptr;
+        std::vector<std::pair<int64_t, int64_t>> groups;  // (first work entry, entries)
+    } fl[4];
+    uint64_t flow_launches = 0;
 
     static int slot(int b) { return b == 64 ? 0 : b == 128 ? 1 : b == 512 ? 3 : 2; }
 
@@ -1236,6 +1249,11 @@ struct steps_batch {
         for (auto &w : work) {
             if (w.graph) cudaGraphExecDestroy(w.graph);
             cudaFree(w.d);
+        }
+        for (auto &f : fl) {
+            cudaFree(f.d_tnb_off);
+            cudaFree(f.d_tnb);
+            cudaFree(f.d_flow);
         }
         cudaFree(d_reps);
         cudaFree(d_err);
@@ -1307,10 +1325,107 @@ struct steps_batch {
         return rc;
     }
 
+    // the flow tables of block size b (once; build_work(b) first)
+    int build_flow(int b) {
+        Flow &f = fl[slot(b)];
+        if (f.d_flow) return STEPS_OK;
+        int dev = 0, l2 = 0;
+        if (!cuda_ok(cudaGetDevice(&dev), "steps_batch: device") ||
+            !cuda_ok(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev), "steps_batch: L2 size"))
+            return STEPS_ERR_CUDA;
+        std::vector<int32_t> off, nb, tmp;
+        std::vector<std::pair<int64_t, int64_t>> groups;
+        int64_t nwork = 0;
+        try {
+            int64_t gfirst = 0, gbytes = 0;
+            for (steps_sim *m : members) {
+                const int64_t B = b, T = m->T, tiles = (T + B - 1) / B, base = nwork;
+                // counts (both buffers) and tables the member's windows touch
+                const int64_t bytes = T * (8 * (int64_t)m->S + 40) + (m->d_rmask ? 4 * T : 0);
+                if (nwork > gfirst && gbytes + bytes > (int64_t)l2 / 2) {
+                    groups.emplace_back(gfirst, nwork - gfirst);
+                    gfirst = nwork;
+                    gbytes = 0;
+                }
+                gbytes += bytes;
+                for (int64_t t = 0; t < tiles; ++t) {
+                    tmp.assign(1, (int32_t)(base + t));
+                    for (int64_t d = t * B; d < std::min(T, (t + 1) * B); ++d)
+                        for (int q = 0; q < 4; ++q) {
+                            const int32_t j = m->tab.nbr_dev[(size_t)(4 * d + q)];
+                            if (j >= 0 && j / B != t) tmp.push_back((int32_t)(base + j / B));
+                        }
+                    std::sort(tmp.begin(), tmp.end());
+                    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+                    off.push_back((int32_t)nb.size());
+                    nb.insert(nb.end(), tmp.begin(), tmp.end());
+                }
+                nwork += tiles;
+            }
+            off.push_back((int32_t)nb.size());
+            if (nwork > gfirst) groups.emplace_back(gfirst, nwork - gfirst);
+        } catch (const std::bad_alloc &) {
+            set_error("steps_batch: flow tables: out of host memory");
+            return STEPS_ERR_OOM;
+        }
+        if (nwork != work[slot(b)].n) {
+            set_error("steps_batch: flow tables do not match the work list");
+            return STEPS_ERR_STATE;
+        }
+        if (!cuda_ok(cudaMalloc((void **)&f.d_tnb_off, off.size() * 4), "steps_batch: flow tables") ||
+            !cuda_ok(cudaMalloc((void **)&f.d_tnb, nb.size() * 4), "steps_batch: flow tables") ||
+            !cuda_ok(cudaMalloc((void **)&f.d_flow, ((size_t)nwork + 1) * 4), "steps_batch: flow tables")) {
+            cudaFree(f.d_tnb_off);
+            cudaFree(f.d_tnb);
+            cudaFree(f.d_flow);
+            f.d_tnb_off = f.d_tnb = nullptr;
+            f.d_flow = nullptr;
+            return STEPS_ERR_OOM;
+        }
+        if (!cuda_ok(cudaMemcpy(f.d_tnb_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice), "steps_batch") ||
+            !cuda_ok(cudaMemcpy(f.d_tnb, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice), "steps_batch") ||
+            !cuda_ok(cudaMemset(f.d_flow, 0, ((size_t)nwork + 1) * 4), "steps_batch"))
+            return STEPS_ERR_CUDA;
+        f.groups = std::move(groups);
+        return STEPS_OK;
+    }
+
+    // n full windows of every member as flow launches, one per group (the
+    // device member table is not advanced: the table of any later window
+    // is uploaded from the host)
+    int flow_windows(int b, int64_t n) {
+        int rc = build_flow(b);
+        if (rc) return rc;
+        Flow &f = fl[slot(b)];
+        for (const auto &g : f.groups) {
+            const int64_t cap = std::max<int64_t>(1, (int64_t)0x7FFFFFFF / g.second);
+            for (int64_t done = 0; done < n;) {
+                const int64_t nw = std::min(n - done, cap);
+                if (!cuda_ok(cudaMemsetAsync(f.d_flow + work[slot(b)].n, 0, 4, stream), "steps_batch: flow counter"))
+                    return STEPS_ERR_CUDA;
+                FlowArgs a;
+                a.tnb_off = f.d_tnb_off;
+                a.tnb = f.d_tnb;
+                a.tile_done = f.d_flow;
+                a.fetch = f.d_flow + work[slot(b)].n;
+                a.nwin = (uint32_t)nw;
+                a.ntiles = (uint32_t)g.second;
+                rc = launch_spec_batch_flow(spec[slot(b)], work[slot(b)].d, d_reps, a, (uint32_t)g.first, max_S, b,
+                                            stream);
+                if (rc) return rc;
+                ++launches;
+                ++flow_launches;
+                done += nw;
+            }
+        }
+        return STEPS_OK;
+    }
+
     int run_windows(int b, int64_t n) {  // n windows at block size b
         int rc = build_work(b);
         if (!rc) rc = prepare_spec(b);
         if (rc) return rc;
+        if (flow && use_spec && spec[slot(b)] && n >= 2) return flow_windows(b, n);
         int64_t done = 0;
         if (use_graph && n >= kGraphWindows) {
             rc = graph_for(b);
@@ -1358,6 +1473,11 @@ int steps_batch_create(steps_sim *const *members, int32_t n, const steps_batch_o
     b->autotune = o.block == 0;
     b->block = o.block == 0 ? 256 : o.block;
     b->use_graph = o.use_graph != 0;
+    if (o.flow != 0 && o.flow != 1) {
+        set_error("steps_batch_create: flow must be 0 (window launches, default) or 1 (group flow launches)");
+        return STEPS_ERR_ARG;
+    }
+    b->flow = o.flow == 1;
     b->stream = (cudaStream_t)cuda_stream;
     for (int32_t j = 0; j < n; ++j) {
         if (!members[j]) {

@@ -80,6 +80,10 @@ int launch_spec(void *spec, const ModelDev &m, const StepArgs &a, int block, voi
 // Full windows a.window .. a.window + f.nwin - 1 in one persistent launch of
 // the flow kernel (one block per resident slot); f.fetch must be zero.
 int launch_spec_flow(void *spec, const ModelDev &m, const StepArgs &a, const FlowArgs &f, int block, void *stream);
+// Full windows of the batch members whose tiles are work[work0 .. work0 + f.ntiles) in one launch of
+// the batched flow kernel (f.nwin windows from each member's current window); f.fetch must be zero.
+int launch_spec_batch_flow(void *spec, const BlockWork *work, RepEntry *reps, const FlowArgs &f, uint32_t work0, int S,
+                           int block, void *stream);
 int launch_spec_batch(void *spec, const BlockWork *work, int64_t nblocks, RepEntry *reps, int S, int block,
                       void *stream);
 std::string spec_program_source(const HostModel &hm, int block);

@@ -161,6 +161,11 @@ std::string program_source(const HostModel &hm, int block) {
       << "int32_t prefetch) {\n"
       << "    steps::batch_tile<" << block << ", " << reaction_bucket(hm.dev.R) << ", steps::SpecModel>(work, reps, "
       << "prefetch);\n}\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << 2048 / block / 2 << ")\n"
+      << "steps_spec_batch_flow(const steps::BlockWork *__restrict__ work, const steps::RepEntry *__restrict__ reps, "
+      << "const __grid_constant__ steps::FlowArgs f, uint32_t work0, int32_t prefetch) {\n"
+      << "    steps::batch_flow_tile<" << block << ", " << reaction_bucket(hm.dev.R) << ", steps::SpecModel>(work, reps, "
+      << "f, work0, prefetch);\n}\n";
     return o.str();
 }
 
@@ -168,9 +173,11 @@ struct Compiled {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;        // plain step kernel
     cudaKernel_t kern_batch = nullptr;  // batched step kernel
-    cudaKernel_t kern_flow = nullptr;   // persistent kernel of a simulation's full windows
+    cudaKernel_t kern_flow = nullptr;   // flow kernel of a simulation's full windows
+    cudaKernel_t kern_batch_flow = nullptr;  // flow kernel of a group of batch members
     size_t smem_set = 0;                // dynamic shared memory the plain kernel was opted in to
     size_t smem_set_flow = 0;           // the flow kernel
+    size_t smem_set_batch_flow = 0;     // the batched flow kernel
     size_t smem_set_batch = 0;          // and the batched one
     bool global_trial = false;          // trial counts in StepArgs::trial, not shared memory
 };
@@ -233,7 +240,8 @@ Compiled *compiled(const HostModel &hm, int block, std::string *why) {
     if (cudaLibraryLoadData(&c->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
         cudaLibraryGetKernel(&c->kern, c->lib, "steps_spec_step") != cudaSuccess ||
         cudaLibraryGetKernel(&c->kern_batch, c->lib, "steps_spec_batch") != cudaSuccess ||
-        cudaLibraryGetKernel(&c->kern_flow, c->lib, "steps_spec_flow") != cudaSuccess) {
+        cudaLibraryGetKernel(&c->kern_flow, c->lib, "steps_spec_flow") != cudaSuccess ||
+        cudaLibraryGetKernel(&c->kern_batch_flow, c->lib, "steps_spec_batch_flow") != cudaSuccess) {
         cudaGetLastError();
         if (why) *why = "loading the compiled kernel failed";
         g_cache[src] = nullptr;
@@ -316,6 +324,25 @@ int launch_spec_flow(void *spec, const ModelDev &m, const StepArgs &a, const Flo
     cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3((unsigned)block), args, smem, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         set_error(std::string("flow step kernel launch: ") + cudaGetErrorString(e));
+        return STEPS_ERR_CUDA;
+    }
+    return STEPS_OK;
+}
+
+int launch_spec_batch_flow(void *spec, const BlockWork *work, RepEntry *reps, const FlowArgs &f, uint32_t work0, int S,
+                           int block, void *stream) {
+    if (f.nwin == 0 || f.ntiles == 0) return STEPS_OK;
+    Compiled *c = static_cast<Compiled *>(spec);
+    const void *fn = (const void *)c->kern_batch_flow;
+    const size_t smem = ((size_t)S + 1 + (c->global_trial ? 0 : (size_t)S)) * (size_t)block * sizeof(int32_t);
+    if (!opt_in(fn, smem, &c->smem_set_batch_flow)) return STEPS_ERR_CUDA;
+    int32_t prefetch = prefetch_distance(fn, block, smem);
+    FlowArgs ff = f;
+    void *args[5] = {(void *)&work, (void *)&reps, (void *)&ff, (void *)&work0, (void *)&prefetch};
+    const unsigned grid = f.nwin * f.ntiles;  // one item per block
+    cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3((unsigned)block), args, smem, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("batched flow step kernel launch: ") + cudaGetErrorString(e));
         return STEPS_ERR_CUDA;
     }
     return STEPS_OK;

@@ -613,12 +613,15 @@ __device__ __forceinline__ bool flow_deps_wait(const FlowArgs &f, uint32_t t, ui
     return ok;
 }
 
-// FLOW: the block takes its item (window q, tile) from f's counter instead
-// (a launch of several windows, flow_tiles). Returns false when the tile's
-// copies or the tiles it depends on did not arrive within the wait limits.
-template <int BLOCK, int RM, class P, bool FLOW = false>
+// FLOW (a launch of several windows): 1, the block takes its item (window
+// q, tile) from f's counter (flow_tiles); 2, the caller took it and passes q
+// and the tile's index among f's tiles, dep (batch_flow_tile). Tile `tile`
+// of window a.window + q then waits for the tiles listed for dep and
+// publishes dep when done. Returns false when the tile's copies or the tiles
+// it depends on did not arrive within the wait limits.
+template <int BLOCK, int RM, class P, int FLOW = 0>
 __device__ __forceinline__ bool step_tile(const ModelDev &m, const StepArgs &a, int64_t tile,
-                                          const FlowArgs *f = nullptr) {
+                                          const FlowArgs *f = nullptr, uint32_t q = 0, uint32_t dep = 0) {
     extern __shared__ __align__(16) int32_t smem[];  // cnt [S + 1][BLOCK], trial [S][BLOCK]
     __shared__ __align__(16) uint4 s_thr[BLOCK];
     __shared__ __align__(16) int4 s_nbr[BLOCK];
@@ -652,18 +655,18 @@ __device__ __forceinline__ bool step_tile(const ModelDev &m, const StepArgs &a, 
         ncalm = 0;
         next_chunk = 0;
         mbar_init(&bar, 1);
-        if constexpr (FLOW) s_item = atomicAdd(f->fetch, 1u);
+        if constexpr (FLOW == 1) s_item = atomicAdd(f->fetch, 1u);
     }
     P::template build<BLOCK>(m, tb);
     if (tid < S) s_scale[tid] = a.scale[tid];
     __syncthreads();
     // the window of this tile: q windows after a.window (buffers swapped when q is odd)
-    uint32_t q = 0;
-    if constexpr (FLOW) {
+    if constexpr (FLOW == 1) {
         const uint32_t item = s_item;
         if (item >= f->nwin * f->ntiles) return true;
         q = item / f->ntiles;
         tile = (int64_t)(item - q * f->ntiles);
+        dep = (uint32_t)tile;
     }
     int32_t *const cur = (q & 1u) ? a.nxt : a.cur;
     int32_t *const nxt = (q & 1u) ? a.cur : a.nxt;
@@ -703,8 +706,8 @@ __device__ __forceinline__ bool step_tile(const ModelDev &m, const StepArgs &a, 
     // it to complete (and its memory to be visible); in a flow launch, for the
     // tiles this one depends on
     bool deps = true;
-    if constexpr (FLOW) {
-        if (q > 0 && tid < 32) deps = flow_deps_wait(*f, (uint32_t)tile, (uint32_t)(a.window + q));
+    if constexpr (FLOW != 0) {
+        if (q > 0 && tid < 32) deps = flow_deps_wait(*f, dep, (uint32_t)(a.window + q));
     } else {
         asm volatile("griddepcontrol.wait;" ::: "memory");
     }
@@ -958,10 +961,10 @@ __device__ __forceinline__ bool step_tile(const ModelDev &m, const StepArgs &a, 
         }
     }
     if (bad) atomicOr(a.err, bad);
-    if constexpr (FLOW) {
+    if constexpr (FLOW != 0) {
         // publish: every thread's writes of this tile come before the release
         __syncthreads();
-        if (tid == 0) st_release_gpu(f->tile_done + tile, (uint32_t)(a.window + q + 1));
+        if (tid == 0) st_release_gpu(f->tile_done + dep, (uint32_t)(a.window + q + 1));
     }
     return true;
 }
@@ -980,7 +983,7 @@ __device__ __forceinline__ bool step_tile(const ModelDev &m, const StepArgs &a, 
 // number of resident blocks.
 template <int BLOCK, int RM, class P>
 __device__ __forceinline__ void flow_tiles(const ModelDev &m, const StepArgs &a, const FlowArgs &f) {
-    step_tile<BLOCK, RM, P, true>(m, a, 0, &f);
+    step_tile<BLOCK, RM, P, 1>(m, a, 0, &f);
 }
 
 // One block of a batched launch: the member named by work[blockIdx.x] copies
@@ -1012,6 +1015,53 @@ __device__ __forceinline__ void batch_tile(const BlockWork *__restrict__ work, c
     }
     __syncthreads();
     step_tile<BLOCK, RM, P>(t_model, t_args, (int64_t)t_tile);
+}
+
+// Full windows of a group of batch members in one launch (the batched form of
+// flow_tiles). The group's tiles are work[work0 .. work0 + f.ntiles), member
+// by member; item (q, i) is tile work0 + i of window q of its member (its own
+// window index and buffers). A member whose windows end earlier skips its
+// later items; nothing depends on them (the dependencies stay within a
+// member). f's tile lists and words are indexed by work entry.
+template <int BLOCK, int RM, class P>
+__device__ __forceinline__ void batch_flow_tile(const BlockWork *__restrict__ work, const RepEntry *__restrict__ reps,
+                                                const FlowArgs &f, uint32_t work0, int32_t prefetch) {
+    __shared__ __align__(16) ModelDev t_model;
+    __shared__ __align__(16) StepArgs t_args;
+    __shared__ uint32_t s_q, s_dep;
+    __shared__ int32_t s_rep, s_tile;
+    if (threadIdx.x == 0) {
+        const uint32_t item = atomicAdd(f.fetch, 1u);
+        s_rep = -1;
+        if (item < f.nwin * f.ntiles) {
+            const uint32_t q = item / f.ntiles, i = item - q * f.ntiles;
+            const BlockWork bw = work[work0 + i];
+            if (reps[bw.rep].args.window + q < reps[bw.rep].window_end) {
+                s_rep = bw.rep;
+                s_tile = bw.tile;
+                s_q = q;
+                s_dep = work0 + i;
+            }
+        }
+    }
+    __syncthreads();
+    if (s_rep < 0) return;
+    const RepEntry *e = reps + s_rep;
+    static_assert(sizeof(ModelDev) % 4 == 0 && sizeof(StepArgs) % 4 == 0, "word copy");
+    const uint32_t *src_m = reinterpret_cast<const uint32_t *>(&e->model);
+    uint32_t *dst_m = reinterpret_cast<uint32_t *>(&t_model);
+    for (int k = threadIdx.x; k < (int)(sizeof(ModelDev) / 4); k += BLOCK) dst_m[k] = src_m[k];
+    const uint32_t *src_a = reinterpret_cast<const uint32_t *>(&e->args);
+    uint32_t *dst_a = reinterpret_cast<uint32_t *>(&t_args);
+    for (int k = threadIdx.x; k < (int)(sizeof(StepArgs) / 4); k += BLOCK) dst_a[k] = src_a[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        t_args.cur = e->cnt[e->parity];
+        t_args.nxt = e->cnt[e->parity ^ 1u];
+        t_args.prefetch = prefetch;  // tiles ahead within the member
+    }
+    __syncthreads();
+    step_tile<BLOCK, RM, P, 2>(t_model, t_args, (int64_t)s_tile, &f, s_q, s_dep);
 }
 
 }  // namespace

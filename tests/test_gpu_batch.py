@@ -193,3 +193,33 @@ def test_batch_tables_survive_a_busy_stream(capi):
         for j, (m, s) in enumerate(zip(members, alone)):
             assert m.windows == s.windows and m.time == s.time, (r, j)
             assert np.array_equal(m.get_counts(), s.get_counts()), (r, j)
+
+
+def test_batch_flow_groups_equal_window_launches(capi):
+    """The batched flow form: members of one model structure with different
+    mesh spacings (so different windows and window counts: members that end
+    earlier skip their later items), about 1.3M tets in all (more than one
+    L2-sized group), over a run that ends off every member's window grid and
+    a second one. Every member equals the same batch in window launches and,
+    for a sample, the member run alone."""
+    hs = [10 / 17, 10 / 15, 10 / 19, 10 / 17, 10 / 13, 10 / 21, 10 / 17, 10 / 16]
+    ws = [I.config2(seed=300 + j, nx=[200, 30, 130, 110, 17, 80, 6, 70][j], h=h * I.UM, t_end=2.1e-3)
+          for j, h in enumerate(hs)]
+    out = {}
+    for flow in (True, False):
+        members = [capi.from_workload(w) for w in ws]
+        b = capi.Batch(members, block=256, specialize=1, flow=flow)
+        b.run([1.7e-3 + 0.05e-3 * j for j in range(len(ws))])
+        b.run([w.t_end for w in ws])
+        assert b.specialized
+        out[flow] = [(m.get_counts(), m.windows, m.time) for m in members]
+        b.close()
+    assert sum(len(w.tets) for w in ws) > 1_000_000
+    assert len({o[1] for o in out[True]}) > 1  # members take different numbers of windows
+    for (a, wa, ta), (c, wc, tc) in zip(out[True], out[False]):
+        assert wa == wc and ta == tc and np.array_equal(a, c)
+    for j in (1, 4, 6):
+        s = capi.from_workload(ws[j])
+        s.run(1.7e-3 + 0.05e-3 * j)
+        s.run(ws[j].t_end)
+        assert np.array_equal(s.get_counts(), out[True][j][0])
