@@ -6,6 +6,8 @@
 #include <cstring>
 #include <limits>
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -61,6 +63,16 @@ __global__ void any_negative(const int32_t *src, int64_t n, uint32_t *flag) {
         neg |= src[i] < 0;
     if (__any_sync(0xFFFFFFFFu, neg) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
+
+// Launch-form choices of tuned simulations, shared by every simulation of
+// the same compiled kernel, tet count and block size (clones of one
+// prototype, the jobs of a stream): the first one's tuning run decides.
+struct FlowChoice {
+    int pick;
+    float ms[3];
+};
+std::mutex g_flow_mu;
+std::map<std::tuple<const void *, int64_t, int>, FlowChoice> g_flow_choice;
 
 bool cuda_ok(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return true;
@@ -338,6 +350,16 @@ struct steps_sim {
     // fastest flow form is kept when it is more than 2 % faster than window
     // launches. The windows taken are ordinary windows of the run.
     int tune_flow(int64_t *used) {
+        const auto key = std::make_tuple((const void *)spec, T, opt.block);
+        {
+            std::lock_guard<std::mutex> lock(g_flow_mu);
+            auto it = g_flow_choice.find(key);
+            if (it != g_flow_choice.end()) {
+                flow_pick = it->second.pick;
+                std::memcpy(flow_ms, it->second.ms, sizeof(flow_ms));
+                return STEPS_OK;
+            }
+        }
         int rc = ensure_flow(0);
         if (!rc && opt.block < 512) rc = ensure_flow(1);
         if (rc) return rc;
@@ -376,6 +398,11 @@ struct steps_sim {
             if (tot[c] < tot[best]) best = c;
         for (int c = 0; c < nc; ++c) flow_ms[c] = tot[c] / (2.f * (float)g);
         flow_pick = tot[best] < 0.98f * tot[0] ? best : 0;
+        std::lock_guard<std::mutex> lock(g_flow_mu);
+        FlowChoice ch;
+        ch.pick = flow_pick;
+        std::memcpy(ch.ms, flow_ms, sizeof(flow_ms));
+        g_flow_choice[key] = ch;
         return STEPS_OK;
     }
 
