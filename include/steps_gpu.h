@@ -64,6 +64,7 @@ typedef struct steps_sim steps_sim;
 /* Internal tet order. */
 #define STEPS_REORDER_NONE 0
 #define STEPS_REORDER_MORTON 1 /* Morton (Z-order) of barycentres (default) */
+#define STEPS_REORDER_RCM 2    /* reverse Cuthill-McKee of the face adjacency (face neighbours a few positions apart) */
 
 typedef struct steps_options {
     int32_t occupancy;   /* STEPS_OCC_MEAN or STEPS_OCC_END */

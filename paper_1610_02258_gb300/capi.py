@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsteps_gpu.so")
 
 STEPS_OCC_MEAN, STEPS_OCC_END = 1, 0
-STEPS_REORDER_NONE, STEPS_REORDER_MORTON = 0, 1
+STEPS_REORDER_NONE, STEPS_REORDER_MORTON, STEPS_REORDER_RCM = 0, 1, 2
 STEPS_LEAVE_EULER, STEPS_LEAVE_EXP = 0, 1
 
 ERRORS = {-1: "STEPS_ERR_ARG", -2: "STEPS_ERR_MESH", -3: "STEPS_ERR_MODEL", -4: "STEPS_ERR_OOM",

@@ -560,6 +560,11 @@ int steps_sim_create(const steps_mesh *mesh, const steps_model *model, uint64_t 
             set_error("steps_sim_create: bad leave law");
             return STEPS_ERR_ARG;
         }
+        if (s->opt.reorder != STEPS_REORDER_NONE && s->opt.reorder != STEPS_REORDER_MORTON &&
+            s->opt.reorder != STEPS_REORDER_RCM) {
+            set_error("steps_sim_create: bad reorder");
+            return STEPS_ERR_ARG;
+        }
         if (s->opt.flow < -1 || s->opt.flow > 1) {
             set_error("steps_sim_create: flow must be 0 (tuned), 1 (on) or -1 (off)");
             return STEPS_ERR_ARG;
@@ -1109,7 +1114,7 @@ int steps_debug_host_tables(const steps_mesh *mesh, const steps_model *model, in
     CHECK_NULL(model, "steps_debug_host_tables");
     CHECK_NULL(tau, "steps_debug_host_tables");
     CHECK_NULL(thr, "steps_debug_host_tables");
-    if (reorder != STEPS_REORDER_NONE && reorder != STEPS_REORDER_MORTON) {
+    if (reorder != STEPS_REORDER_NONE && reorder != STEPS_REORDER_MORTON && reorder != STEPS_REORDER_RCM) {
         set_error("steps_debug_host_tables: bad reorder");
         return STEPS_ERR_ARG;
     }

@@ -163,3 +163,46 @@ def test_host_tables_equal_the_oracle(capi, case):
         assert d_morton < 0.1 * d_orig
     else:
         assert d_morton < 2.0 * d_orig
+
+
+@pytest.mark.parametrize("case", ["box", "dendrite", "two_parts"])
+def test_rcm_order_is_a_narrow_band_permutation(capi, case):
+    """Reverse Cuthill-McKee order: a permutation of the tets, deterministic,
+    with the same tau and thresholds as Morton order, and
+    face neighbours a few positions apart: the largest distance is the
+    band of the breadth-first levels, far below Morton order's on the
+    dendrite. two_parts: two disconnected meshes (two components)."""
+    import oracle
+    if case == "box":
+        w = I.config2(nx=5)
+        verts, tets = w.verts, w.tets
+    elif case == "dendrite":
+        w = I.config3(h=0.45e-6)
+        verts, tets = w.verts, w.tets
+    else:
+        w = I.config1()
+        verts, tets = I.replicate_mesh(w.verts, w.tets, 2, spacing=5e-6)
+    nt = len(tets)
+    mesh = capi.steps_mesh_create(verts, tets)
+    model = capi.steps_model_create(w.model.diff, w.model.lhs, w.model.rhs, w.model.k)
+    try:
+        tau_r, thr_r, perm_r = capi.steps_debug_host_tables(mesh, model, nt, reorder=capi.STEPS_REORDER_RCM)
+        tau_r2, _, perm_r2 = capi.steps_debug_host_tables(mesh, model, nt, reorder=capi.STEPS_REORDER_RCM)
+        tau_m, thr_m, perm_m = capi.steps_debug_host_tables(mesh, model, nt, reorder=capi.STEPS_REORDER_MORTON)
+    finally:
+        capi.steps_model_destroy(model)
+        capi.steps_mesh_destroy(mesh)
+    assert np.array_equal(np.sort(perm_r), np.arange(nt)) and np.array_equal(perm_r, perm_r2)
+    assert tau_r == tau_r2 == tau_m
+    assert np.array_equal(thr_r, thr_m)  # per tet, in the caller's order: the order does not change them
+    nbr, *_ = oracle.geometry(verts, tets)
+    i, f = np.nonzero(nbr >= 0)
+
+    def band(perm):
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(nt)
+        return np.abs(inv[nbr[i, f]] - inv[i]).max()
+
+    assert band(perm_r) <= band(perm_m)
+    if case == "dendrite":
+        assert band(perm_r) * 20 < band(perm_m)

@@ -133,3 +133,46 @@ def test_flow_dendrite_full_size_equals_window_launches(capi):
         out.append(g.get_counts())
         g.close()
     assert np.array_equal(out[0], out[1])
+
+
+def test_flow_edge_sizes(capi):
+    """Flow launches on a single isolated tet (infinite tau: no full window,
+    so nothing flows and the run equals the oracle), and on small boxes of
+    108, 384 and 768 tets with 256- and 512-tet tiles: one partial tile, two
+    tiles with a ragged last one, exactly three full tiles, one and a half
+    tiles; with the box's counts and with none."""
+    verts, tets = I.isolated_tets(1)
+    m = I.config1_model()
+    c = np.array([[3], [4], [0]], np.int32)
+    g = capi.Simulation(verts, tets, m, 5, specialize=1, flow=True)
+    g.set_counts(c)
+    o = oracle.OracleSim(verts, tets, m, seed=5, prec=32)
+    o.set_counts(c)
+    g.run(1e-2)
+    o.run(1e-2)
+    assert np.array_equal(g.get_counts(), o.get_counts()) and g.windows == o.windows
+    for nx, ny, nz in ((2, 3, 3), (4, 4, 4), (8, 4, 4)):
+        w = I.config2(nx=nx, ny=ny, nz=nz, t_end=2e-3)
+        assert len(w.tets) == 6 * nx * ny * nz
+        for block in (256, 512):
+            for counts in (w.counts, np.zeros_like(w.counts)):
+                g = capi.Simulation(w.verts, w.tets, w.model, w.seed, specialize=1, flow=True, block=block)
+                g.set_counts(counts)
+                o = oracle.OracleSim(w.verts, w.tets, w.model, seed=w.seed, prec=32)
+                o.set_counts(counts)
+                g.run(w.t_end)
+                o.run(w.t_end)
+                assert g.flow[0] == block
+                assert g.windows == o.windows and np.array_equal(g.get_counts(), o.get_counts()), (nx, block)
+                g.close()
+
+
+@pytest.mark.parametrize("flow", [True, False])
+def test_rcm_order_keeps_the_bits(capi, flow):
+    """Reverse Cuthill-McKee tet order, in flow launches and window launches,
+    on the calcium network with its masked influx: the oracle's counts (the
+    draws are keyed by the caller's tet ids, so the order changes nothing)."""
+    w = I.config3(h=0.5e-6, t_end=0.2e-3)
+    g, o = _both(capi, w, [0.07e-3, w.t_end], masks=w.reac_masks, specialize=1, flow=flow,
+                 reorder=capi.STEPS_REORDER_RCM)
+    assert bool(g.flow[0]) == flow

@@ -105,7 +105,7 @@ def test_logf_bit_exact_on_every_uniform(capi):
 
 # ------------------------------------------------------------------ whole runs, bit-exact
 
-@pytest.mark.parametrize("reorder", [0, 1])
+@pytest.mark.parametrize("reorder", [0, 1, 2])
 def test_pure_diffusion_bit_exact(capi, reorder):
     """Diffusion only (no reactions): integer work end to end, including the
     shortened last window."""
