@@ -88,9 +88,10 @@ struct StepArgs {
     uint32_t scale[kMaxSpecies];  // per-species fixed-point scale for this window length
 };
 
-// Full windows of one simulation in one persistent launch (flow_tiles): the
-// items are (window q, tile t), q-major; the item (q, t) waits until every
-// tile sharing a face with t, t included, has finished window q - 1.
+// Full windows of one simulation in one flow launch (flow_tiles; the batched
+// form: a group of members, batch_flow_tile): one block per item (window q,
+// tile t), q-major; the item (q, t) waits until every tile sharing a face
+// with t, t included, has finished window q - 1.
 struct FlowArgs {
     const int32_t *tnb_off;  // [ntiles + 1] offsets into tnb of each tile's neighbour tiles
     const int32_t *tnb;      // neighbour tiles (each tile lists itself)

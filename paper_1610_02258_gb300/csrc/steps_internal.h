@@ -77,8 +77,8 @@ int launch_advance(RepEntry *reps, int32_t n, void *stream);
 // nullptr (with the reason in *why) when they cannot be built.
 void *spec_kernel(const HostModel &hm, int block, std::string *why);
 int launch_spec(void *spec, const ModelDev &m, const StepArgs &a, int block, void *stream);
-// Full windows a.window .. a.window + f.nwin - 1 in one persistent launch of
-// the flow kernel (one block per resident slot); f.fetch must be zero.
+// Full windows a.window .. a.window + f.nwin - 1 in one launch of the flow
+// kernel (one block per item: f.nwin x f.ntiles blocks); f.fetch must be zero.
 int launch_spec_flow(void *spec, const ModelDev &m, const StepArgs &a, const FlowArgs &f, int block, void *stream);
 // Full windows of the batch members whose tiles are work[work0 .. work0 + f.ntiles) in one launch of
 // the batched flow kernel (f.nwin windows from each member's current window); f.fetch must be zero.

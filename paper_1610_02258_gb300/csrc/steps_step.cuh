@@ -555,24 +555,6 @@ __device__ __forceinline__ void apply_remaining(const ModelDev &m, const StepArg
 }
 
 
-// One diffusion window for BLOCK consecutive tets (device order).
-//  load   counts and tables into shared memory by bulk copies; each thread
-//         notes its tet's non-zero species and zeroes their entries in `cur`
-//         (which receives the window after next)
-//  A      each thread: its tet's propensities (reactions no tet of the warp
-//         can fire are skipped warp-wide: their propensity is 0) and first
-//         waiting time, in float; (double)dt > tau_k is tested as
-//         dt > tau_dn, tau_dn the largest float <= tau_k (the same decision);
-//         a tet whose first event falls inside the window fires it here and
-//         is listed as reacting, the others holding molecules as calm
-//  chunks each warp takes chunks of 32 listed tets (reacting tets first):
-//         the reacting tets' SSA from their second event on; trial counts;
-//         the chunk's Philox blocks of trial words (each word moves or keeps
-//         one trial molecule; movers are added to the neighbour's entry of
-//         `nxt` at once), spread over the warp's lanes for calm chunks and
-//         over the whole block, after a barrier, for chunks with reacting
-//         tets; then each tet's remaining counts are added to its own entry
-//         of `nxt`. Z: the model has order-0 reactions.
 __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -613,6 +595,24 @@ __device__ __forceinline__ bool flow_deps_wait(const FlowArgs &f, uint32_t t, ui
     return ok;
 }
 
+// One diffusion window for BLOCK consecutive tets (device order).
+//  load   counts and tables into shared memory by bulk copies; each thread
+//         notes its tet's non-zero species and zeroes their entries in `cur`
+//         (which receives the window after next)
+//  A      each thread: its tet's propensities (reactions no tet of the warp
+//         can fire are skipped warp-wide: their propensity is 0) and first
+//         waiting time, in float; (double)dt > tau_k is tested as
+//         dt > tau_dn, tau_dn the largest float <= tau_k (the same decision);
+//         a tet whose first event falls inside the window fires it here and
+//         is listed as reacting, the others holding molecules as calm
+//  chunks each warp takes chunks of 32 listed tets (reacting tets first):
+//         the reacting tets' SSA from their second event on; trial counts;
+//         the chunk's Philox blocks of trial words (each word moves or keeps
+//         one trial molecule; movers are added to the neighbour's entry of
+//         `nxt` at once), spread over the warp's lanes for calm chunks and
+//         over the whole block, after a barrier, for chunks with reacting
+//         tets; then each tet's remaining counts are added to its own entry
+//         of `nxt`. Z: the model has order-0 reactions.
 // FLOW (a launch of several windows): 1, the block takes its item (window
 // q, tile) from f's counter (flow_tiles); 2, the caller took it and passes q
 // and the tile's index among f's tiles, dep (batch_flow_tile). Tile `tile`
