@@ -75,14 +75,15 @@ typedef struct steps_options {
                             least 65,536 tets and NVRTC is available (default), 1 = always (sim creation fails
                             with STEPS_ERR_CUDA if it cannot be built), -1 = never (the generic kernel) */
     int32_t leave_law;   /* STEPS_LEAVE_EULER (default) or STEPS_LEAVE_EXP */
-    int32_t flow;        /* launch form of a run's consecutive full windows on the model-specialised kernel.
-                            Flow: one launch for all of them, in which each tile of a window starts as soon as
-                            the tiles holding its face neighbours have finished the previous window. Window
-                            launches: one launch per window (graph replay as use_graph says). 0 (default): the
-                            first run with at least 72 full windows times, on its own windows, window launches,
-                            flow launches of `block`-tet tiles and (when block < 512) of 512-tet tiles, and keeps
-                            the fastest (steps_sim_flow reports it); 1: flow at `block`; -1: window launches.
-                            The results are the same bits in every form. */
+    int32_t flow;        /* launch form of a run's consecutive full windows. Flow: one launch for all of them,
+                            in which each tile of a window starts as soon as the tiles holding its face
+                            neighbours have finished the previous window (the model-specialised kernel at any
+                            block size, the generic kernel at block 256). Window launches: one launch per
+                            window (graph replay as use_graph says). 0 (default): the first run with at least
+                            72 full windows times, on its own windows, window launches, flow launches of
+                            `block`-tet tiles and (specialised, block < 512) of 512-tet tiles, and keeps the
+                            fastest (steps_sim_flow reports it); 1: flow at `block` where a flow kernel exists;
+                            -1: window launches. The results are the same bits in every form. */
     int32_t reserved[1]; /* set to 0 */
 } steps_options;
 

@@ -126,7 +126,8 @@ struct steps_sim {
     // `block` tets in device order, CSR), the tiles' finished-window words and
     // the item counter (d_flow[ntiles]).
     struct Flow {
-        void *spec = nullptr;
+        void *spec = nullptr;  // null with `generic`: the generic kernel's flow form (256-thread blocks)
+        bool generic = false;
         int block = 0;
         bool tried = false;
         int32_t *d_tnb_off = nullptr;
@@ -166,15 +167,18 @@ struct steps_sim {
     }
 
     // flow[k]'s kernel and tables (once): tile t lists itself and every tile
-    // holding a face neighbour of one of its tets. flow[1]'s kernel is
-    // compiled here; if that fails, flow[1].spec stays null (no candidate).
+    // holding a face neighbour of one of its tets. flow[0] runs the
+    // simulation's kernel (the generic one only at 256-thread blocks);
+    // flow[1], 512-tet tiles of the specialised kernel, is compiled here. A
+    // form without a kernel keeps no tables (d_flow null: no candidate).
     int ensure_flow(int k) {
         Flow &fl = flow[k];
         if (fl.d_flow || fl.tried) return STEPS_OK;
         fl.tried = true;
         const int64_t B = k == 0 ? opt.block : 512;
-        void *sp = k == 0 ? spec : spec_kernel(model, 512, nullptr);
-        if (!sp) return STEPS_OK;
+        void *sp = k == 0 ? spec : (spec ? spec_kernel(model, 512, nullptr) : nullptr);
+        const bool generic = k == 0 && !spec;
+        if (!sp && !(generic && B == 256)) return STEPS_OK;
         const int64_t nt = (T + B - 1) / B;
         std::vector<int32_t> off, nb, tmp;
         try {
@@ -211,6 +215,7 @@ struct steps_sim {
             !cuda_ok(cudaMemset(fl.d_flow, 0, ((size_t)nt + 1) * 4), "flow tables"))
             return STEPS_ERR_CUDA;
         fl.spec = sp;
+        fl.generic = generic;
         fl.block = (int)B;
         fl.ntiles = nt;
         fl.bytes = (off.size() + nb.size() + (size_t)nt + 1) * 4;
@@ -326,21 +331,25 @@ struct steps_sim {
         return rc;
     }
 
+    // a flow kernel exists for the simulation's block size
+    bool flow_possible() const { return spec || opt.block == 256; }
+
     // n full windows: flow launches or window launches (all give the same bits)
     int full_windows(int64_t n) {
-        if (spec && opt.flow == 0 && flow_pick < 0 && n >= kFlowTuneWindows) {
+        if (opt.flow == 0 && flow_pick < 0 && flow_possible() && n >= kFlowTuneWindows) {
             int64_t used = 0;
             int rc = tune_flow(&used);
             if (rc) return rc;
             n -= used;
         }
         int k = -1;
-        if (spec && n >= 2) {
+        if (n >= 2 && flow_possible()) {
             if (opt.flow == 1) k = 0;
             else if (opt.flow == 0 && flow_pick >= 1) k = flow_pick - 1;
         }
         return k >= 0 ? flow_windows(n, k) : window_launches(n);
     }
+
 
     // The first run with enough full windows times the launch forms on
     // alternating groups of windows: window launches, flow launches at the
@@ -363,7 +372,7 @@ struct steps_sim {
         int rc = ensure_flow(0);
         if (!rc && opt.block < 512) rc = ensure_flow(1);
         if (rc) return rc;
-        const int nc = flow[0].spec ? (flow[1].spec ? 3 : 2) : 1;
+        const int nc = flow[0].d_flow ? (flow[1].d_flow ? 3 : 2) : 1;
         if (nc == 1) {
             flow_pick = 0;
             return STEPS_OK;
@@ -440,7 +449,7 @@ struct steps_sim {
         int rc = ensure_flow(k);
         if (rc) return rc;
         const Flow &fl = flow[k];
-        if (!fl.spec) return window_launches(n);
+        if (!fl.d_flow) return window_launches(n);
         const int64_t ntiles = fl.ntiles;
         uint32_t *const d_flow = fl.d_flow;
         const int64_t cap = std::max<int64_t>(1, (int64_t)0x7FFFFFFF / ntiles);
@@ -455,7 +464,8 @@ struct steps_sim {
             f.fetch = d_flow + ntiles;
             f.nwin = (uint32_t)nw;
             f.ntiles = (uint32_t)ntiles;
-            rc = launch_spec_flow(fl.spec, model.dev, a, f, fl.block, stream);
+            rc = fl.generic ? launch_flow(model.dev, a, f, fl.block, stream)
+                            : launch_spec_flow(fl.spec, model.dev, a, f, fl.block, stream);
             if (rc) return rc;
             ++launches;
             done += nw;
@@ -1045,7 +1055,7 @@ int steps_sim_flow(const steps_sim *sim, int32_t *flow_block, float *tune_ms) {
     CHECK_NULL(sim, "steps_sim_flow");
     CHECK_NULL(flow_block, "steps_sim_flow");
     int k = -1;
-    if (sim->spec) {
+    if (sim->flow_possible()) {
         if (sim->opt.flow == 1) k = 0;
         else if (sim->opt.flow == 0 && sim->flow_pick >= 1) k = sim->flow_pick - 1;
     }

@@ -80,6 +80,8 @@ int launch_spec(void *spec, const ModelDev &m, const StepArgs &a, int block, voi
 // Full windows a.window .. a.window + f.nwin - 1 in one launch of the flow
 // kernel (one block per item: f.nwin x f.ntiles blocks); f.fetch must be zero.
 int launch_spec_flow(void *spec, const ModelDev &m, const StepArgs &a, const FlowArgs &f, int block, void *stream);
+// The same on the generic step kernel (block must be 256).
+int launch_flow(const ModelDev &m, const StepArgs &a, const FlowArgs &f, int block, void *stream);
 // Full windows of the batch members whose tiles are work[work0 .. work0 + f.ntiles) in one launch of
 // the batched flow kernel (f.nwin windows from each member's current window); f.fetch must be zero.
 int launch_spec_batch_flow(void *spec, const BlockWork *work, RepEntry *reps, const FlowArgs &f, uint32_t work0, int S,

@@ -14,6 +14,15 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK / 2)
     step_tile<BLOCK, RM, RtModel<Z>>(m, a, (int64_t)blockIdx.x);
 }
 
+// The flow form of the generic kernel (256-thread blocks only): one block per
+// item (window, tile) of a run's full windows.
+template <int RM, bool Z>
+__global__ void __launch_bounds__(256, 4)
+    flow_kernel(const __grid_constant__ ModelDev m, const __grid_constant__ StepArgs a,
+                const __grid_constant__ FlowArgs f) {
+    flow_tiles<256, RM, RtModel<Z>>(m, a, f);
+}
+
 __global__ void philox_test_kernel(uint32_t k0, uint32_t k1, const uint4 *ctr, int64_t n, uint4 *out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -118,6 +127,42 @@ int launch_step_b(const ModelDev &m, const StepArgs &a, void *stream) {
     return m.order0 ? launch_step_z<BLOCK, true>(m, a, stream) : launch_step_z<BLOCK, false>(m, a, stream);
 }
 
+template <int RM, bool Z>
+int launch_flow_t(const ModelDev &m, const StepArgs &a, const FlowArgs &f, void *stream) {
+    const size_t smem = (2 * (size_t)m.S + 1) * 256 * sizeof(int32_t);
+    static size_t static_smem = [] {
+        cudaFuncAttributes fa{};
+        return cudaFuncGetAttributes(&fa, flow_kernel<RM, Z>) == cudaSuccess ? fa.sharedSizeBytes : (size_t)0;
+    }();
+    if (smem + static_smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(flow_kernel<RM, Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            set_error(std::string("flow kernel shared memory: ") + cudaGetErrorString(e));
+            return STEPS_ERR_CUDA;
+        }
+    }
+    StepArgs b = a;
+    b.window_base = nullptr;
+    // the item taken about half a resident wave later: its tables into L2
+    if (b.prefetch) b.prefetch = prefetch_distance(reinterpret_cast<const void *>(flow_kernel<RM, Z>), 256, smem);
+    const unsigned grid = f.nwin * f.ntiles;  // one item per block
+    flow_kernel<RM, Z><<<grid, 256, smem, (cudaStream_t)stream>>>(m, b, f);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("flow kernel launch: ") + cudaGetErrorString(e));
+        return STEPS_ERR_CUDA;
+    }
+    return STEPS_OK;
+}
+
+template <bool Z>
+int launch_flow_z(const ModelDev &m, const StepArgs &a, const FlowArgs &f, void *stream) {
+    if (m.R <= 8) return launch_flow_t<8, Z>(m, a, f, stream);
+    if (m.R <= 16) return launch_flow_t<16, Z>(m, a, f, stream);
+    if (m.R <= 24) return launch_flow_t<24, Z>(m, a, f, stream);
+    return launch_flow_t<32, Z>(m, a, f, stream);
+}
+
 }  // namespace
 
 int prefetch_distance(const void *kernel, int block, size_t smem) {
@@ -157,6 +202,15 @@ int launch_philox_test(uint64_t seed, const uint32_t *d_ctr, int64_t n, uint32_t
     philox_test_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
         (uint32_t)seed, (uint32_t)(seed >> 32), (const uint4 *)d_ctr, n, (uint4 *)d_out);
     return cudaGetLastError() == cudaSuccess ? STEPS_OK : STEPS_ERR_CUDA;
+}
+
+int launch_flow(const ModelDev &m, const StepArgs &a, const FlowArgs &f, int block, void *stream) {
+    if (a.T <= 0 || f.nwin == 0) return STEPS_OK;
+    if (block != 256) {
+        set_error("flow launches of the generic step kernel need 256-thread blocks");
+        return STEPS_ERR_ARG;
+    }
+    return m.order0 ? launch_flow_z<true>(m, a, f, stream) : launch_flow_z<false>(m, a, f, stream);
 }
 
 int launch_wait_test(const void *d_src, int deliver, long long limit, uint32_t *d_status, void *stream) {

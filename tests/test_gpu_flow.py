@@ -176,3 +176,20 @@ def test_rcm_order_keeps_the_bits(capi, flow):
     g, o = _both(capi, w, [0.07e-3, w.t_end], masks=w.reac_masks, specialize=1, flow=flow,
                  reorder=capi.STEPS_REORDER_RCM)
     assert bool(g.flow[0]) == flow
+
+
+@pytest.mark.parametrize("which", ["cuboid", "box"])
+def test_generic_kernel_flow_bit_exact(capi, which):
+    """The generic kernel's flow form (meshes below the specialisation size),
+    forced: the cuboid's 8 tiles over 13 full windows and a shortened one;
+    the 10-species box of 20,808 tets (82 tiles) over stops that leave odd
+    window counts. By default these short runs take window launches."""
+    if which == "cuboid":
+        w, t_ends = I.config1(), [3e-3, 10e-3]
+    else:
+        w, t_ends = I.config2(nx=12, t_end=3e-3), [0.21e-3 * 3 + 1e-6, 3e-3]
+    g, o = _both(capi, w, t_ends, specialize=-1, flow=True)
+    assert not g.specialized and g.flow[0] == 256
+    assert o.events > 0
+    g, _ = _both(capi, w, t_ends, specialize=-1)
+    assert g.flow[0] == 0
