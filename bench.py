@@ -162,15 +162,16 @@ def launch_form(sim):
     return (f"flow{block}_kernel" if block else "step_kernel"), keys
 
 
-def issue_roofline(tr, kernel_s: float, sm_mhz):
+def issue_roofline(tr, kernel_s: float, sm_mhz, sms=None):
     """Warp instructions issued per second by the kernel (count per launch from
     the ncu capture, time per launch measured here) against the issue peak:
     SMs x 4 schedulers x 1 warp instruction per cycle x the SM clock sampled
     during the run."""
     if not tr or "warp_instructions_per_launch" not in tr:
         return None
-    import torch
-    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    if sms is None:
+        import torch
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = sm_mhz or 2070.0
     peak = sms * 4 * mhz * 1e6
     achieved = tr["warp_instructions_per_launch"] / kernel_s
@@ -260,7 +261,7 @@ def cpu_baseline_dendrite(I, windows_all: int, windows_one: int):
 
 
 def roofline(S: int, masked: bool, tets: int, kernel_s: float, peak: float, peak_kind: str, tr, sm_mhz,
-             issue_bound: bool):
+             issue_bound: bool, sms=None):
     """Roofline object of a plain step launch. hbm: algorithmic bytes per
     tet-update, 8S + 52 (counts in and out, neighbours, FP64 split tables,
     FP64 tau G, the volume factor) and the 8S + 36 (+4 with reaction masks)
@@ -274,7 +275,7 @@ def roofline(S: int, masked: bool, tets: int, kernel_s: float, peak: float, peak
            "achieved_fixed_point": tets * b36 / kernel_s / 1e9, "frac_fixed_point": tets * b36 / kernel_s / 1e9 / peak,
            "bytes_per_tet_update_fixed_point": b36, "peak_source": peak_kind,
            "traffic": tr["bytes_per_launch"] if tr else None, "kernel_us_avg": kernel_s * 1e6}
-    iss = issue_roofline(tr, kernel_s, sm_mhz)
+    iss = issue_roofline(tr, kernel_s, sm_mhz, sms)
     if issue_bound and iss is not None:
         out = {"bound": "alu", "achieved": iss["achieved"], "peak": iss["peak"], "unit": "warp-inst/s",
                "frac": iss["frac"], "traffic": hbm["traffic"],
